@@ -1,0 +1,368 @@
+"""Benchmark of the Moebius domain-wall hopping kernel (Dhop) on GB300.
+
+Workload: Moebius DWF (M5 = 1.8, b = 1.5, c = 0.5) Dhop at 32^3 x 64 x Ls = 12,
+FP32 storage, one right-hand side, links U = exp(i 0.3 H), Gaussian source,
+seed 5.  One step = one application of Dhop to the whole 5D field (the paper's
+"Domain Wall kernel", 1320 flop per 5D site update, Table 3).
+
+Prints one JSON line: throughput in GFlop/s (1320-flop convention), the HBM
+roofline of the kernel against the measured copy bandwidth, an end-to-end
+figure through the host-buffer C entry point, the CPU oracle as a baseline,
+and the SM clocks sampled during the timed region.  The fused D, D^+ and
+D^+D applies and the FP16-storage Dhop are timed too and reported under "ops".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Möbius DWF Dhop GFlop/s & % HBM roofline; mixed vs FP64 CG time to 1e-10"
+DIMS = (32, 32, 32, 64)
+LS = 12
+M5, B, C = 1.8, 1.5, 0.5
+MF = 0.01
+SEED = 5
+FLOP_DHOP = 1320           # per 5D site update (Table 3)
+FLOP_D_MOBIUS = 1320 + 192  # + (b + cK) on the input (3 x 24) and the diagonal (5 x 24)
+
+
+def bytes_per_site(real_bytes: int, Ls: int, nrhs: int = 1) -> float:
+    """Algorithmic HBM bytes per 5D site update: read psi once (24 reals), write
+    once (24 reals), 4 links x 18 reals per 4D site shared by Ls*nrhs updates."""
+    return real_bytes * (48 + 72.0 / (Ls * nrhs))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper half of the observed clocks
+        loaded = [v for v in sm if v >= 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+
+
+def _max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_op(fn, steps, warmup, stream):
+    """Mean ms per call over `steps` calls with CUDA events on `stream`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_baseline(psi, U, budget_s=12.0):
+    """The FP64 oracle's Dhop on the host cores: whole-lattice applies until the
+    time budget is spent (at least one)."""
+    import oracle
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.dhop(psi, U, DIMS, LS)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = (time.perf_counter() - t0) / n
+    V5 = int(np.prod(DIMS)) * LS
+    return {"value": FLOP_DHOP * V5 / dt / 1e9, "unit": "GFlop/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%d whole-lattice FP64 Dhop apply(s) at 32^3x64xLs12 (%.1f s each)" % (n, dt)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the same workload, each step a bounded
+    sample of the lattice (a fixed set of 4D sites, all slices)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2112_01852_gb300 import inputs
+    oracle.build()
+    V4 = int(np.prod(DIMS))
+    U = inputs.exp_su3_field(DIMS, seed=SEED)
+    psi = inputs.gaussian_fermion(DIMS, LS, 1, seed=SEED)
+    nsite = 65536  # 4D sites per step (x Ls = 786432 site updates)
+    rng = np.random.default_rng(0)
+    sites = np.sort(rng.choice(V4, size=nsite, replace=False))
+    for _ in range(args.warmup):
+        oracle.dhop(psi, U, DIMS, LS, sites=sites)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dhop(psi, U, DIMS, LS, sites=sites)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = FLOP_DHOP * nsite * LS / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GFlop/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(),
+        "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": "%d random 4D sites x Ls=12 per step of the 32^3x64 lattice"
+                                   % nsite},
+        "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config():
+    return {"workload": "mobius_dwf_dhop_32x32x32x64_ls12_f32", "dims": list(DIMS), "Ls": LS,
+            "nrhs": 1, "kind": "mobius", "M5": M5, "b": B, "c": C, "mf": MF,
+            "links": "exp(i 0.3 H)", "seed": SEED, "prec": "f32",
+            "l2": "inputs larger than L2 (2.42 GB FP32 field vs 129 MB L2)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2112_01852_gb300 import build as cuda_build
+    from paper_2112_01852_gb300 import dw, inputs
+    from paper_2112_01852_gb300.lattice import Lattice
+    cuda_build.build()
+
+    V4 = int(np.prod(DIMS))
+    V5 = V4 * LS
+    U = inputs.exp_su3_field(DIMS, seed=SEED)
+    psi = inputs.gaussian_fermion(DIMS, LS, 1, seed=SEED)
+
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    lat = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32)
+    lat.load_gauge(U)
+    x = lat.pack(psi)
+    y = lat.empty(1)
+    tiles = {}
+    for op in (dw.DW_OP_DHOP, dw.DW_OP_D, dw.DW_OP_DDAG):
+        tiles[op] = lat.tune(op, 1)
+
+    def dhop():
+        dw.dw_apply_Dhop(lat.handle, y.data_ptr(), x.data_ptr(), 1, sh)
+
+    # warm-up and timed region (barrier + synchronize on both sides)
+    for _ in range(args.warmup):
+        dhop()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dhop()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = _max_over_ranks(ws, ms)
+    gflops = FLOP_DHOP * V5 / (ms * 1e-3) / 1e9 * ws
+
+    # roofline of the Dhop kernel (one launch per step)
+    peak, peak_kind = _peaks()
+    bps = bytes_per_site(4, LS)
+    alg_bytes = bps * V5
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+
+    # other operators on the same lattice (kernel-only, same event method)
+    mf = [MF]
+    ops = {}
+    ops["D"] = time_op(lambda: dw.dw_apply_D(lat.handle, y.data_ptr(), x.data_ptr(), mf, 1, sh),
+                       args.steps, 3, stream)
+    ops["Ddag"] = time_op(
+        lambda: dw.dw_apply_Ddag(lat.handle, y.data_ptr(), x.data_ptr(), mf, 1, sh),
+        args.steps, 3, stream)
+    ops["DdagD"] = time_op(
+        lambda: dw.dw_apply_DdagD(lat.handle, y.data_ptr(), x.data_ptr(), mf, 1, sh),
+        max(5, args.steps // 2), 3, stream)
+    ops_out = {
+        "D": {"ms": ops["D"], "gflops": FLOP_D_MOBIUS * V5 / ops["D"] / 1e6,
+              "gbs": alg_bytes / ops["D"] / 1e6},
+        "Ddag": {"ms": ops["Ddag"], "gflops": FLOP_D_MOBIUS * V5 / ops["Ddag"] / 1e6,
+                 "gbs": alg_bytes / ops["Ddag"] / 1e6},
+        "DdagD": {"ms": ops["DdagD"], "gflops": 2 * FLOP_D_MOBIUS * V5 / ops["DdagD"] / 1e6,
+                  "gbs": 2 * alg_bytes / ops["DdagD"] / 1e6},
+        "tiles": {"Dhop": tiles[dw.DW_OP_DHOP], "D": tiles[dw.DW_OP_D],
+                  "Ddag": tiles[dw.DW_OP_DDAG]},
+    }
+    # FP16-storage Dhop on the same lattice
+    lat16 = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F16)
+    lat16.load_gauge(U)
+    x16 = lat16.pack(psi)
+    y16 = lat16.empty(1)
+    lat16.tune(dw.DW_OP_DHOP, 1)
+    ms16 = time_op(lambda: dw.dw_apply_Dhop(lat16.handle, y16.data_ptr(), x16.data_ptr(), 1, sh),
+                   args.steps, 3, stream)
+    ops_out["Dhop_f16"] = {"ms": ms16, "gflops": FLOP_DHOP * V5 / ms16 / 1e6,
+                           "gbs": bytes_per_site(2, LS) * V5 / ms16 / 1e6,
+                           "frac": bytes_per_site(2, LS) * V5 / ms16 / 1e6 / peak}
+    del x16, y16
+    lat16.close()
+
+    # end to end through the host-buffer entry point (pinned host, H2D + D2H inside)
+    nbytes = lat.fermion_bytes(1)
+    hin = x.cpu().pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    lat.apply_host(dw.DW_OP_DHOP, hout, hin)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.apply_host(dw.DW_OP_DHOP, hout, hin)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = _max_over_ranks(ws, e2e_s)
+    e2e = {"value": FLOP_DHOP * V5 / e2e_s / 1e9 * ws, "unit": "GFlop/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "ms_per_step": e2e_s * 1e3}
+
+    line = {
+        "metric": METRIC, "value": gflops, "unit": "GFlop/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": _config(),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind,
+                     "bytes_per_site": bps, "sites_per_launch": V5},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "ops": ops_out,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(psi, U)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

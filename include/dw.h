@@ -1,0 +1,190 @@
+/*
+ * dw.h -- C ABI of the GB300 domain-wall fermion operator library (libdw_gb300.so).
+ *
+ * The library applies the domain-wall fermion operator in its Shamir and Moebius
+ * forms on one GPU.  Its hot part is the "Domain Wall kernel" of the paper
+ * (Sec. 4.1): the 4D Wilson hopping term applied to every fifth-dimension slice,
+ * i.e. per 5D site spin projection to a half spinor, SU(3) x half spinor and
+ * reconstruction (Table 3, 1320 flop per site update).  The paper names the
+ * operator but does not write it down; the definitions used here are
+ *
+ *   Dhop psi(x,s) = sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu,s) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu,s) ]
+ *   D_W   = (4 - M5) - Dhop / 2
+ *   K psi_s = P- psi_{s+1} + P+ psi_{s-1}; at the walls -mf P- psi_0 (s = Ls-1) and
+ *             -mf P+ psi_{Ls-1} (s = 0); P+- = (1 +- g5) / 2
+ *   D     = D_W (b + c K) + (1 - K)           Shamir: b = 1, c = 0
+ *   D^+   = (b + c K^+) D_W^+ + (1 - K^+)
+ *
+ * with chiral-basis gammas g_k = [[0, i s_k], [-i s_k, 0]], g_4 = [[0, 1], [1, 0]],
+ * g5 = diag(1, 1, -1, -1), and a factor bc[mu] on every hop that crosses the
+ * lattice edge in direction mu.
+ *
+ * Conventions common to every call
+ *  - Field buffers are caller-owned DEVICE pointers (unless the name says _host)
+ *    in the library's internal layout (see dw_fermion_bytes), at the lattice's
+ *    precision, 16-byte aligned.  Several right-hand sides are stored back to
+ *    back, each dw_fermion_bytes(lat, prec, 1) long.
+ *  - All calls are ordered on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) and asynchronous, except dw_cg_solve and dw_apply_host, which
+ *    synchronise.
+ *  - No C++ exception crosses the ABI.  Every int-returning call returns DW_OK or
+ *    a negative DW_ERR_* code; dw_last_error() returns the calling thread's last
+ *    message.  A failed argument check launches nothing.
+ *  - `out` must not alias `in`.
+ *
+ * Internal fermion layout (per RHS): planes [p][s][x4] of 16-byte vectors
+ * (8-byte for DW_F16), x4 = x + Lx*(y + Ly*(z + Lz*t)).  The 24 reals of a 5D
+ * site are its 4 spins x 3 colours x (re, im) in canonical order; plane p holds
+ * reals [p*R, p*R + R) with R = 2 (F64) or 4 (F32, F16).  Planes 0 .. 12/R-1 are
+ * the upper (P+) spins, the rest the lower (P-) spins.
+ *
+ * Canonical layout (dw_pack_fermion / dw_unpack_fermion / dw_load_gauge):
+ *   fermion complex128 [rhs][x4][s][spin 4][colour 3]
+ *   gauge   complex128 [x4][mu = x,y,z,t][row 3][col 3], U_mu(x) links x to x+mu.
+ */
+#ifndef DW_GB300_H
+#define DW_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dw_lattice dw_lattice; /* opaque, library-owned */
+
+enum {
+  DW_OK = 0,
+  DW_ERR_ARG = -1,           /* invalid argument (null pointer, size, alignment, enum) */
+  DW_ERR_ALLOC = -2,         /* device allocation failed */
+  DW_ERR_CUDA = -3,          /* a CUDA call failed */
+  DW_ERR_STATE = -4,         /* call out of order (e.g. apply before dw_load_gauge) */
+  DW_ERR_NOT_CONVERGED = -5, /* CG hit maxit; stats still filled */
+  DW_ERR_BREAKDOWN = -6,     /* CG met a non-finite or non-positive <p, A p> */
+  DW_ERR_TIMEOUT = -7        /* a bounded device-side wait gave up */
+};
+
+enum { DW_SHAMIR = 0, DW_MOBIUS = 1 };
+enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2 };
+
+/* Operator selector for dw_apply_host. */
+enum { DW_OP_DHOP = 0, DW_OP_DHOP_DAG = 1, DW_OP_D = 2, DW_OP_DDAG = 3, DW_OP_DDAGD = 4 };
+
+/*
+ * Create a lattice of dims[4] = {Lx, Ly, Lz, Lt} 4D sites x Ls slices.
+ * kind: DW_SHAMIR (b, c ignored and set to 1, 0) or DW_MOBIUS.
+ * prec: storage precision of the fields passed to the dw_apply_* calls
+ *       (DW_F64, DW_F32, or DW_F16 = IEEE binary16 storage with FP32 arithmetic).
+ * bc:   per-direction boundary sign (+1 periodic, -1 antiperiodic); NULL means
+ *       {1, 1, 1, -1}.
+ * Every dim and Ls must be >= 1 and V4 = Lx*Ly*Lz*Lt < 2^31.  The lattice owns
+ * its gauge copies, scratch space and tuning cache; free it with
+ * dw_destroy_lattice.  Uses the current CUDA device.
+ */
+int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, double M5,
+                      double b, double c, int prec, const int bc[4]);
+void dw_destroy_lattice(dw_lattice *lat);
+
+/*
+ * Copy and convert a gauge field (DEVICE pointer, canonical complex128) into
+ * the lattice's internal link arrays at every precision, folding the boundary
+ * signs into the links that cross the lattice edge.  The caller may free U as
+ * soon as the stream has passed this call.
+ */
+int dw_load_gauge(dw_lattice *lat, const void *U, void *stream);
+
+/*
+ * out = Dhop in, the bare hopping sum over the 8 neighbours for every slice s
+ * and each of nrhs right-hand sides (no -1/2 factor, no diagonal term).
+ * This is the paper's Domain Wall kernel (Sec. 4.1; 1320 flop per 5D site,
+ * Table 3).
+ */
+int dw_apply_Dhop(dw_lattice *lat, void *out, const void *in, int nrhs, void *stream);
+/* out = Dhop^+ in  (= g5 Dhop g5 in). */
+int dw_apply_Dhop_dag(dw_lattice *lat, void *out, const void *in, int nrhs, void *stream);
+
+/*
+ * out = D in with the per-RHS masses mf[nrhs] (HOST array).  One fused pass:
+ * (b + cK) is applied to the neighbour spinors before the hop.
+ */
+int dw_apply_D(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+               void *stream);
+/* out = D^+ in. */
+int dw_apply_Ddag(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                  void *stream);
+/*
+ * out = D^+ D in.  The intermediate D in lives in lattice-owned scratch, so
+ * calls on one lattice must not overlap on different streams.
+ */
+int dw_apply_DdagD(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                   void *stream);
+
+/*
+ * Apply operator `op` (DW_OP_*) with HOST buffers in the internal layout at
+ * the lattice precision: copies in to the device, applies, copies out back and
+ * synchronises the stream.  Device staging buffers are lattice-owned.
+ * mf may be NULL for DW_OP_DHOP / DW_OP_DHOP_DAG.
+ */
+int dw_apply_host(dw_lattice *lat, int op, void *out_host, const void *in_host,
+                  const double *mf, int nrhs, void *stream);
+
+typedef struct {
+  int iters;            /* operator applications of the inner solver */
+  int reliable_updates; /* FP64 residual recomputations (mixed modes) */
+  int converged;        /* 1 if true_resid <= tol */
+  double true_resid;    /* |b - D^+D x| / |b| recomputed in FP64 */
+  double seconds;       /* wall time of the whole solve */
+} dw_cg_stats;
+
+/*
+ * Solve D^+D x = b for nrhs right-hand sides with per-RHS masses mf[nrhs]
+ * (HOST array).  x and b are DEVICE fields in the internal layout at DW_F64
+ * (x holds the start vector on entry, the solution on exit).
+ * mode: DW_F64 plain FP64 CG; DW_F32 / DW_F16 mixed precision: the inner
+ * operator runs at FP32 / FP16 storage with FP32 arithmetic, with FP64 reliable
+ * updates, FP64 reductions and an FP64 true-residual convergence test.
+ * Stops when |b - D^+D x| / |b| <= tol for every RHS (converged RHS are masked
+ * off) or after maxit inner iterations.  stats[nrhs] (HOST) is filled.
+ * Returns DW_OK, DW_ERR_NOT_CONVERGED or DW_ERR_BREAKDOWN.  Synchronises.
+ */
+int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs,
+                double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
+
+/*
+ * Stencil-kernel tiles.  A tile is (spt, tx): spt fifth-dimension slices per
+ * thread (1..4, dividing Ls) and tx 4D sites per CTA (a multiple of 32); a CTA
+ * holds all Ls/spt slice groups of its tx sites.
+ *
+ * dw_set_tile pins the tile used for operator `op` (DW_OP_DHOP .. DW_OP_DDAG)
+ * at precision `prec` for launches of `nrhs` right-hand sides (0 = any count
+ * without a more specific entry).  Returns DW_ERR_ARG for an invalid tile.
+ *
+ * dw_tune times every valid tile for (op, nrhs) at the lattice precision on
+ * lattice-owned scratch fields (CUDA events on `stream`, median of a few
+ * launches), keeps the fastest for later calls and returns it in *spt, *tx
+ * (either may be NULL).  Requires a loaded gauge field; synchronises; must not
+ * be called while `stream` is being captured into a graph.
+ */
+int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx);
+int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, void *stream);
+
+/* Bytes of one internal-layout field of nrhs right-hand sides at precision prec. */
+size_t dw_fermion_bytes(const dw_lattice *lat, int prec, int nrhs);
+
+/*
+ * Convert between the canonical complex128 layout (src/dst DEVICE pointer) and
+ * the internal layout at precision prec (rounding to nearest even for F32/F16).
+ */
+int dw_pack_fermion(dw_lattice *lat, void *dst_internal, int prec, const void *src_c128,
+                    int nrhs, void *stream);
+int dw_unpack_fermion(dw_lattice *lat, void *dst_c128, const void *src_internal, int prec,
+                      int nrhs, void *stream);
+
+/* Calling thread's last error message ("" if none). */
+const char *dw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DW_GB300_H */

@@ -1,0 +1,409 @@
+// C ABI of the domain-wall library: lattice lifetime, gauge loading, operator
+// application and field conversion.  Every entry point validates its
+// arguments, never lets a C++ exception escape and reports failures through a
+// negative status plus a thread-local message (dw_last_error).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dw_api_internal.cuh"
+
+namespace dw {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(DW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t field_bytes(const dw_lattice *lat, int prec, int nrhs) {
+  return (size_t)24 * (size_t)lat->V5 * (size_t)prec_real_bytes(prec) * (size_t)nrhs;
+}
+
+FieldGeom geom(const dw_lattice *lat) {
+  FieldGeom g;
+  for (int m = 0; m < 4; ++m) g.L[m] = lat->dims[m];
+  g.V4 = (int)lat->V4;
+  g.Ls = lat->Ls;
+  return g;
+}
+
+int ensure_buffer(void **buf, size_t *cap, size_t need) {
+  if (*cap >= need && *buf) return DW_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(buf, need);
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    cudaGetLastError();
+    return fail(DW_ERR_ALLOC, "cudaMalloc of %zu bytes failed: %s", need, cudaGetErrorString(e));
+  }
+  *cap = need;
+  return DW_OK;
+}
+
+int dslash_max_threads(int prec, int op, int spt) {
+  switch (prec) {
+    case DW_F64: return dslash_max_threads_f64(op, spt);
+    case DW_F32: return dslash_max_threads_f32(op, spt);
+    case DW_F16: return dslash_max_threads_f16(op, spt);
+  }
+  return 0;
+}
+
+// Untuned choice: the smallest slices-per-thread whose CTA of 32 sites x Ls/spt
+// slice groups fits the kernel's register budget, then up to 256 threads.
+TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs) {
+  (void)nrhs;
+  const int Ls = lat->Ls;
+  TileConfig t{0, 32};
+  int maxt = 0;
+  for (int spt : {1, 2, 3, 4}) {
+    if (Ls % spt) continue;
+    const int m = dslash_max_threads(prec, op, spt);
+    if ((Ls / spt) * 32 <= m) {
+      t.spt = spt;
+      maxt = m;
+      break;
+    }
+  }
+  if (!t.spt) {  // nothing fits: report through the launch path
+    t.spt = 1;
+    return t;
+  }
+  const int nchunk = Ls / t.spt;
+  while (t.tx * 2 * nchunk <= 256 && t.tx * 2 * nchunk <= maxt) t.tx *= 2;
+  return t;
+}
+
+TileConfig pick_tile(dw_lattice *lat, int prec, int op, int nrhs) {
+  auto it = lat->tuned.find(std::make_tuple(prec, op, nrhs));
+  if (it != lat->tuned.end()) return it->second;
+  it = lat->tuned.find(std::make_tuple(prec, op, 0));
+  if (it != lat->tuned.end()) return it->second;
+  return default_tile(lat, prec, op, nrhs);
+}
+
+bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
+  if (t.spt < 1 || t.spt > 4 || lat->Ls % t.spt) return false;
+  if (t.tx < 32 || t.tx % 32) return false;
+  const long long threads = (long long)t.tx * (lat->Ls / t.spt);
+  return threads <= 1024 && threads <= dslash_max_threads(prec, op, t.spt);
+}
+
+// Stencil launch over all RHS, in groups of at most kMaxRhsPerLaunch.
+int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
+               const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
+               const int *gate, int gate_stride) {
+  const size_t rhs_bytes = field_bytes(lat, prec, 1);
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
+    const int n = (nrhs - r0) < kMaxRhsPerLaunch ? (nrhs - r0) : kMaxRhsPerLaunch;
+    DslashParams p;
+    memset(&p, 0, sizeof(p));
+    p.out = (char *)out + (size_t)r0 * rhs_bytes;
+    p.in = (const char *)in + (size_t)r0 * rhs_bytes;
+    p.gmain = lat->gmain[prec];
+    p.gtail = lat->gtail[prec];
+    for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
+    p.V4 = (int)lat->V4;
+    p.Ls = lat->Ls;
+    p.plane = lat->V5;
+    p.rhs_stride = lat->V5 * (24 / prec_reals_per_vec(prec));
+    p.nrhs = n;
+    p.gate = gate ? gate + (size_t)r0 * gate_stride : nullptr;
+    p.gate_stride = gate_stride;
+    p.M5 = lat->M5;
+    p.b = lat->b;
+    p.c = lat->c;
+    for (int r = 0; r < n; ++r) p.mf[r] = mf_host ? mf_host[r0 + r] : 0.0;
+    const TileConfig cfg = force ? *force : pick_tile(lat, prec, op, nrhs);
+    int rc;
+    switch (prec) {
+      case DW_F64: rc = launch_dslash_f64(p, op, cfg, st); break;
+      case DW_F32: rc = launch_dslash_f32(p, op, cfg, st); break;
+      case DW_F16: rc = launch_dslash_f16(p, op, cfg, st); break;
+      default: rc = -2;
+    }
+    if (rc == -2) return fail(DW_ERR_ARG, "unsupported tile (spt=%d, tx=%d) for Ls=%d", cfg.spt,
+                              cfg.tx, lat->Ls);
+    if (rc == -3)
+      return fail(DW_ERR_ARG, "tile (spt=%d, tx=%d) exceeds the kernel's threads per CTA",
+                  cfg.spt, cfg.tx);
+    if (rc) return cuda_fail(cudaGetLastError(), "dslash launch");
+  }
+  return DW_OK;
+}
+
+int check_apply(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                bool need_mf) {
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!out || !in) return fail(DW_ERR_ARG, "field pointer is NULL");
+  if (out == in) return fail(DW_ERR_ARG, "out must not alias in");
+  if (!aligned16(out) || !aligned16(in)) return fail(DW_ERR_ARG, "fields must be 16-byte aligned");
+  if (nrhs < 1) return fail(DW_ERR_ARG, "nrhs must be >= 1 (got %d)", nrhs);
+  if (need_mf && !mf) return fail(DW_ERR_ARG, "mf is NULL");
+  if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  return DW_OK;
+}
+
+int apply_op(dw_lattice *lat, int op, void *out, const void *in, const double *mf, int nrhs,
+             cudaStream_t st) {
+  switch (op) {
+    case DW_OP_DHOP: return run_dslash(lat, lat->prec, OP_DHOP, out, in, nullptr, nrhs, st, nullptr);
+    case DW_OP_DHOP_DAG:
+      return run_dslash(lat, lat->prec, OP_DHOP_DAG, out, in, nullptr, nrhs, st, nullptr);
+    case DW_OP_D: return run_dslash(lat, lat->prec, OP_D, out, in, mf, nrhs, st, nullptr);
+    case DW_OP_DDAG: return run_dslash(lat, lat->prec, OP_DDAG, out, in, mf, nrhs, st, nullptr);
+    case DW_OP_DDAGD: {
+      const size_t need = field_bytes(lat, lat->prec, nrhs);
+      int rc = ensure_buffer(&lat->scratch, &lat->scratch_bytes, need);
+      if (rc) return rc;
+      rc = run_dslash(lat, lat->prec, OP_D, lat->scratch, in, mf, nrhs, st, nullptr);
+      if (rc) return rc;
+      return run_dslash(lat, lat->prec, OP_DDAG, out, lat->scratch, mf, nrhs, st, nullptr);
+    }
+  }
+  return fail(DW_ERR_ARG, "unknown operator %d", op);
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+extern "C" {
+
+const char *dw_last_error(void) { return g_last_error.c_str(); }
+
+int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, double M5, double b,
+                      double c, int prec, const int bc[4]) {
+  clear_error();
+  if (!out) return fail(DW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!dims) return fail(DW_ERR_ARG, "dims is NULL");
+  long long V4 = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 1) return fail(DW_ERR_ARG, "dims[%d] = %d must be >= 1", m, dims[m]);
+    V4 *= dims[m];
+    if (V4 >= (1LL << 31)) return fail(DW_ERR_ARG, "4D volume too large");
+  }
+  if (Ls < 1) return fail(DW_ERR_ARG, "Ls = %d must be >= 1", Ls);
+  {
+    bool ok = false;
+    for (int spt : {1, 2, 3, 4})
+      if (Ls % spt == 0 && (Ls / spt) * 32 <= 1024) ok = true;
+    if (!ok) return fail(DW_ERR_ARG, "Ls = %d unsupported (need Ls/spt <= 32 for spt in 1..4)", Ls);
+  }
+  if (kind != DW_SHAMIR && kind != DW_MOBIUS) return fail(DW_ERR_ARG, "unknown kind %d", kind);
+  if (prec != DW_F64 && prec != DW_F32 && prec != DW_F16)
+    return fail(DW_ERR_ARG, "unknown precision %d", prec);
+  if (bc)
+    for (int m = 0; m < 4; ++m)
+      if (bc[m] != 1 && bc[m] != -1) return fail(DW_ERR_ARG, "bc[%d] must be +1 or -1", m);
+  dw_lattice *lat = new (std::nothrow) dw_lattice();
+  if (!lat) return fail(DW_ERR_ALLOC, "host allocation failed");
+  for (int m = 0; m < 4; ++m) {
+    lat->dims[m] = dims[m];
+    lat->bc[m] = bc ? bc[m] : (m == 3 ? -1 : 1);
+  }
+  lat->Ls = Ls;
+  lat->V4 = V4;
+  lat->V5 = V4 * Ls;
+  lat->kind = kind;
+  lat->M5 = M5;
+  lat->b = kind == DW_SHAMIR ? 1.0 : b;
+  lat->c = kind == DW_SHAMIR ? 0.0 : c;
+  lat->prec = prec;
+  cudaGetDevice(&lat->device);
+  cudaDeviceGetAttribute(&lat->num_sms, cudaDevAttrMultiProcessorCount, lat->device);
+  for (int p = 0; p < 3; ++p) {
+    const int R = prec_reals_per_vec(p);
+    const size_t main_bytes = (size_t)4 * (16 / R) * V4 * prec_vec_bytes(p);
+    const size_t tail_bytes = (size_t)4 * V4 * 2 * prec_real_bytes(p);
+    cudaError_t e1 = cudaMalloc(&lat->gmain[p], main_bytes);
+    cudaError_t e2 = cudaMalloc(&lat->gtail[p], tail_bytes);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      cudaGetLastError();
+      dw_destroy_lattice(lat);
+      return fail(DW_ERR_ALLOC, "gauge allocation failed");
+    }
+  }
+  *out = lat;
+  return DW_OK;
+}
+
+void dw_destroy_lattice(dw_lattice *lat) {
+  if (!lat) return;
+  for (int p = 0; p < 3; ++p) {
+    if (lat->gmain[p]) cudaFree(lat->gmain[p]);
+    if (lat->gtail[p]) cudaFree(lat->gtail[p]);
+  }
+  if (lat->scratch) cudaFree(lat->scratch);
+  if (lat->stage_in) cudaFree(lat->stage_in);
+  if (lat->stage_out) cudaFree(lat->stage_out);
+  if (lat->partials) cudaFree(lat->partials);
+  cg_release(lat);
+  delete lat;
+}
+
+int dw_load_gauge(dw_lattice *lat, const void *U, void *stream) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!U) return fail(DW_ERR_ARG, "U is NULL");
+  if (!aligned16(U)) return fail(DW_ERR_ARG, "U must be 16-byte aligned");
+  FieldGeom g = geom(lat);
+  if (load_gauge(g, lat->bc, U, lat->gmain, lat->gtail, (cudaStream_t)stream))
+    return cuda_fail(cudaGetLastError(), "gauge conversion launch");
+  lat->gauge_loaded = true;
+  return DW_OK;
+}
+
+int dw_apply_Dhop(dw_lattice *lat, void *out, const void *in, int nrhs, void *stream) {
+  clear_error();
+  int rc = check_apply(lat, out, in, nullptr, nrhs, false);
+  if (rc) return rc;
+  return apply_op(lat, DW_OP_DHOP, out, in, nullptr, nrhs, (cudaStream_t)stream);
+}
+
+int dw_apply_Dhop_dag(dw_lattice *lat, void *out, const void *in, int nrhs, void *stream) {
+  clear_error();
+  int rc = check_apply(lat, out, in, nullptr, nrhs, false);
+  if (rc) return rc;
+  return apply_op(lat, DW_OP_DHOP_DAG, out, in, nullptr, nrhs, (cudaStream_t)stream);
+}
+
+int dw_apply_D(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+               void *stream) {
+  clear_error();
+  int rc = check_apply(lat, out, in, mf, nrhs, true);
+  if (rc) return rc;
+  return apply_op(lat, DW_OP_D, out, in, mf, nrhs, (cudaStream_t)stream);
+}
+
+int dw_apply_Ddag(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                  void *stream) {
+  clear_error();
+  int rc = check_apply(lat, out, in, mf, nrhs, true);
+  if (rc) return rc;
+  return apply_op(lat, DW_OP_DDAG, out, in, mf, nrhs, (cudaStream_t)stream);
+}
+
+int dw_apply_DdagD(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                   void *stream) {
+  clear_error();
+  int rc = check_apply(lat, out, in, mf, nrhs, true);
+  if (rc) return rc;
+  return apply_op(lat, DW_OP_DDAGD, out, in, mf, nrhs, (cudaStream_t)stream);
+}
+
+int dw_apply_host(dw_lattice *lat, int op, void *out_host, const void *in_host, const double *mf,
+                  int nrhs, void *stream) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!out_host || !in_host) return fail(DW_ERR_ARG, "host buffer is NULL");
+  if (op < DW_OP_DHOP || op > DW_OP_DDAGD) return fail(DW_ERR_ARG, "unknown operator %d", op);
+  const bool need_mf = op >= DW_OP_D;
+  if (need_mf && !mf) return fail(DW_ERR_ARG, "mf is NULL");
+  if (nrhs < 1) return fail(DW_ERR_ARG, "nrhs must be >= 1");
+  if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  const size_t bytes = field_bytes(lat, lat->prec, nrhs);
+  size_t cap_in = lat->stage_bytes, cap_out = lat->stage_bytes;
+  int rc = ensure_buffer(&lat->stage_in, &cap_in, bytes);
+  if (rc) return rc;
+  rc = ensure_buffer(&lat->stage_out, &cap_out, bytes);
+  if (rc) return rc;
+  lat->stage_bytes = cap_in < cap_out ? cap_in : cap_out;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(lat->stage_in, in_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  rc = apply_op(lat, op, lat->stage_out, lat->stage_in, mf, nrhs, st);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(out_host, lat->stage_out, bytes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return DW_OK;
+}
+
+int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
+  if (prec < DW_F64 || prec > DW_F16) return fail(DW_ERR_ARG, "unknown precision %d", prec);
+  if (nrhs < 0) return fail(DW_ERR_ARG, "nrhs must be >= 0");
+  TileConfig t{spt, tx};
+  if (!tile_valid(lat, prec, op, t))
+    return fail(DW_ERR_ARG, "invalid tile spt=%d tx=%d for Ls=%d (slices per thread must divide Ls, "
+                "tx a multiple of 32, CTA within the kernel's thread limit)", spt, tx, lat->Ls);
+  lat->tuned[std::make_tuple(prec, op, nrhs)] = t;
+  return DW_OK;
+}
+
+int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, void *stream) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
+  if (nrhs < 1) return fail(DW_ERR_ARG, "nrhs must be >= 1");
+  if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return fail(DW_ERR_STATE, "dw_tune called on a capturing stream");
+  int rc = tune_tile(lat, op, nrhs, st);
+  if (rc) return rc;
+  const TileConfig t = pick_tile(lat, lat->prec, op, nrhs);
+  if (spt) *spt = t.spt;
+  if (tx) *tx = t.tx;
+  return DW_OK;
+}
+
+size_t dw_fermion_bytes(const dw_lattice *lat, int prec, int nrhs) {
+  if (!lat || nrhs < 0 || prec < DW_F64 || prec > DW_F16) return 0;
+  return field_bytes(lat, prec, nrhs);
+}
+
+int dw_pack_fermion(dw_lattice *lat, void *dst_internal, int prec, const void *src_c128, int nrhs,
+                    void *stream) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!dst_internal || !src_c128) return fail(DW_ERR_ARG, "field pointer is NULL");
+  if (prec < DW_F64 || prec > DW_F16) return fail(DW_ERR_ARG, "unknown precision %d", prec);
+  if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
+  if (!aligned16(dst_internal) || !aligned16(src_c128))
+    return fail(DW_ERR_ARG, "fields must be 16-byte aligned");
+  if (pack_fermion(geom(lat), prec, dst_internal, src_c128, nrhs, (cudaStream_t)stream))
+    return cuda_fail(cudaGetLastError(), "pack launch");
+  return DW_OK;
+}
+
+int dw_unpack_fermion(dw_lattice *lat, void *dst_c128, const void *src_internal, int prec,
+                      int nrhs, void *stream) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!dst_c128 || !src_internal) return fail(DW_ERR_ARG, "field pointer is NULL");
+  if (prec < DW_F64 || prec > DW_F16) return fail(DW_ERR_ARG, "unknown precision %d", prec);
+  if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
+  if (!aligned16(dst_c128) || !aligned16(src_internal))
+    return fail(DW_ERR_ARG, "fields must be 16-byte aligned");
+  if (unpack_fermion(geom(lat), prec, dst_c128, src_internal, nrhs, (cudaStream_t)stream))
+    return cuda_fail(cudaGetLastError(), "unpack launch");
+  return DW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,31 @@
+// Internal helpers shared by the C-ABI translation units.
+#pragma once
+
+#include "dw_common.cuh"
+#include "dw_fields.cuh"
+
+namespace dw {
+
+int fail(int code, const char *fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char *what);
+size_t field_bytes(const dw_lattice *lat, int prec, int nrhs);
+FieldGeom geom(const dw_lattice *lat);
+int ensure_buffer(void **buf, size_t *cap, size_t need);
+TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs);
+TileConfig pick_tile(dw_lattice *lat, int prec, int op, int nrhs);
+bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t);
+int dslash_max_threads(int prec, int op, int spt);
+// Time all valid tiles for (op, nrhs) at the lattice precision; store the best.
+int tune_tile(dw_lattice *lat, int op, int nrhs, cudaStream_t st);
+// Stencil launch (op = OpKind) at precision `prec` over nrhs RHS; mf_host may be
+// NULL for the hopping-only kinds; `force` overrides the tile choice.
+// `gate` (optional) skips the CTAs of RHS r unless gate[r * gate_stride] != 0.
+int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
+               const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
+               const int *gate = nullptr, int gate_stride = 0);
+int apply_op(dw_lattice *lat, int op, void *out, const void *in, const double *mf, int nrhs,
+             cudaStream_t st);
+void cg_release(dw_lattice *lat);
+
+}  // namespace dw

@@ -1,0 +1,64 @@
+// BLAS-1 and scalar kernels of the batched conjugate gradient.
+#pragma once
+
+#include "dw_common.cuh"
+
+namespace dw {
+
+constexpr int kBlasThreads = 256;
+
+// Per-RHS solver state, resident on the device for the whole solve.  The
+// int fields come first so that `run` and `need_update` can gate kernels
+// through a strided int pointer.
+struct CGState {
+  int run;          // iterating: active && !need_update (gates the inner operator)
+  int need_update;  // waiting for a reliable update / true-residual check
+  int active;       // not yet converged, stopped or broken down
+  int converged;
+  int breakdown;
+  int iters;
+  int reliable;
+  int pad;
+  double rr;        // |r_s|^2 of the normalised residual
+  double pAp;
+  double alpha;
+  double beta;
+  double sigma;     // scale of the normalised system: true residual = sigma * r_s
+  double maxr;      // largest |r_s| since the last reliable update
+  double bnorm;     // |b|
+  double true_r2;   // last recomputed |b - A x|^2
+  double sigma_next;
+  double beta_next;
+};
+
+constexpr int kCGStateInts = sizeof(CGState) / sizeof(int);
+
+struct BlasCtx {
+  long long V5;
+  int nrhs;
+  int nblk;  // blocks per RHS of the reduction kernels
+  BlasCtx(long long V5_, int nrhs_, int num_sms);
+};
+
+int blas_redot(const BlasCtx &c, int pa, const void *a, int pb, const void *b, double *partial,
+               const CGState *st, cudaStream_t s);
+int blas_finalize_sum(const BlasCtx &c, const double *partial, double *out, cudaStream_t s);
+int cg_residual(const BlasCtx &c, double *r, const double *b, const double *Ax, double *partial,
+                const CGState *st, cudaStream_t s);
+int cg_accumulate_x(const BlasCtx &c, int pr, void *x, const void *x_s, const CGState *st,
+                    cudaStream_t s);
+int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r_s, void *x_s,
+                      void *p, const CGState *st, cudaStream_t s);
+int cg_update(const BlasCtx &c, int pp, int pr, void *x_s, void *r_s, const void *p,
+              const void *Ap, double *partial, const CGState *st, cudaStream_t s);
+int cg_direction(const BlasCtx &c, int pp, int pr, void *p, const void *r_s, const CGState *st,
+                 cudaStream_t s);
+int cg_alpha(const BlasCtx &c, const double *partial, CGState *st, cudaStream_t s);
+int cg_beta(const BlasCtx &c, const double *partial, CGState *st, double delta, double tol,
+            int maxit, cudaStream_t s);
+int cg_reliable(const BlasCtx &c, const double *partial, CGState *st, double tol, int maxit,
+                int first, cudaStream_t s);
+int cg_install(const BlasCtx &c, CGState *st, cudaStream_t s);
+int cg_clear_update(const BlasCtx &c, CGState *st, cudaStream_t s);
+
+}  // namespace dw

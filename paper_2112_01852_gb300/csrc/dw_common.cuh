@@ -1,0 +1,216 @@
+// Common definitions of the GB300 domain-wall library: precision traits, vector
+// load/convert helpers, kernel parameter blocks and the lattice object.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "dw.h"
+
+namespace dw {
+
+// ---------------------------------------------------------------------------
+// Precision traits.  A fermion plane element is one `vec`: 2 doubles (F64),
+// 4 floats (F32) or 4 halves (F16).  `C` is the arithmetic type.  Links keep
+// their first 16 reals in `vec` planes and the last 2 in a `tvec` plane.
+struct F64 {
+  using vec = double2;
+  using tvec = double2;
+  using C = double;
+  static constexpr int R = 2;
+  static constexpr int RB = 8;  // bytes per real
+  static constexpr int id = DW_F64;
+};
+struct F32 {
+  using vec = float4;
+  using tvec = float2;
+  using C = float;
+  static constexpr int R = 4;
+  static constexpr int RB = 4;
+  static constexpr int id = DW_F32;
+};
+struct F16 {
+  using vec = uint2;         // 4 x binary16
+  using tvec = unsigned int; // 2 x binary16
+  using C = float;
+  static constexpr int R = 4;
+  static constexpr int RB = 2;
+  static constexpr int id = DW_F16;
+};
+
+inline int prec_vec_bytes(int prec) { return prec == DW_F64 ? 16 : (prec == DW_F32 ? 16 : 8); }
+inline int prec_reals_per_vec(int prec) { return prec == DW_F64 ? 2 : 4; }
+inline int prec_real_bytes(int prec) { return prec == DW_F64 ? 8 : (prec == DW_F32 ? 4 : 2); }
+
+// ---------------------------------------------------------------------------
+// Device helpers: load a vec through the read-only path and widen to C.
+__device__ __forceinline__ void widen(const double2 &v, double *r) {
+  r[0] = v.x;
+  r[1] = v.y;
+}
+__device__ __forceinline__ void widen(const float4 &v, float *r) {
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+  r[3] = v.w;
+}
+__device__ __forceinline__ void widen(const uint2 &v, float *r) {
+  __half2 a = *reinterpret_cast<const __half2 *>(&v.x);
+  __half2 b = *reinterpret_cast<const __half2 *>(&v.y);
+  float2 fa = __half22float2(a);
+  float2 fb = __half22float2(b);
+  r[0] = fa.x;
+  r[1] = fa.y;
+  r[2] = fb.x;
+  r[3] = fb.y;
+}
+__device__ __forceinline__ void widen_t(const double2 &v, double *r) { widen(v, r); }
+__device__ __forceinline__ void widen_t(const float2 &v, float *r) {
+  r[0] = v.x;
+  r[1] = v.y;
+}
+__device__ __forceinline__ void widen_t(const unsigned int &v, float *r) {
+  __half2 a = *reinterpret_cast<const __half2 *>(&v);
+  float2 fa = __half22float2(a);
+  r[0] = fa.x;
+  r[1] = fa.y;
+}
+
+__device__ __forceinline__ double2 narrow_vec(const double *r, double2 *) {
+  return make_double2(r[0], r[1]);
+}
+__device__ __forceinline__ float4 narrow_vec(const float *r, float4 *) {
+  return make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ uint2 narrow_vec(const float *r, uint2 *) {
+  __half2 a = __floats2half2_rn(r[0], r[1]);
+  __half2 b = __floats2half2_rn(r[2], r[3]);
+  uint2 v;
+  v.x = *reinterpret_cast<unsigned int *>(&a);
+  v.y = *reinterpret_cast<unsigned int *>(&b);
+  return v;
+}
+__device__ __forceinline__ double2 narrow_tvec(const double *r, double2 *) {
+  return make_double2(r[0], r[1]);
+}
+__device__ __forceinline__ float2 narrow_tvec(const float *r, float2 *) {
+  return make_float2(r[0], r[1]);
+}
+__device__ __forceinline__ unsigned int narrow_tvec(const float *r, unsigned int *) {
+  __half2 a = __floats2half2_rn(r[0], r[1]);
+  return *reinterpret_cast<unsigned int *>(&a);
+}
+
+// Rounding straight from double (one rounding step, nearest even) for the
+// layout converters that read canonical FP64 data.
+__device__ __forceinline__ double2 narrow_from_f64(const double *r, double2 *) {
+  return make_double2(r[0], r[1]);
+}
+__device__ __forceinline__ float4 narrow_from_f64(const double *r, float4 *) {
+  return make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
+}
+__device__ __forceinline__ uint2 narrow_from_f64(const double *r, uint2 *) {
+  __half h[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) h[k] = __double2half(r[k]);
+  uint2 v;
+  v.x = (unsigned)__half_as_ushort(h[0]) | ((unsigned)__half_as_ushort(h[1]) << 16);
+  v.y = (unsigned)__half_as_ushort(h[2]) | ((unsigned)__half_as_ushort(h[3]) << 16);
+  return v;
+}
+__device__ __forceinline__ double2 narrow_t_from_f64(const double *r, double2 *) {
+  return make_double2(r[0], r[1]);
+}
+__device__ __forceinline__ float2 narrow_t_from_f64(const double *r, float2 *) {
+  return make_float2((float)r[0], (float)r[1]);
+}
+__device__ __forceinline__ unsigned int narrow_t_from_f64(const double *r, unsigned int *) {
+  return (unsigned)__half_as_ushort(__double2half(r[0])) |
+         ((unsigned)__half_as_ushort(__double2half(r[1])) << 16);
+}
+
+template <class P>
+__device__ __forceinline__ void load_vec(typename P::C *r, const typename P::vec *p) {
+  widen(__ldg(p), r);
+}
+template <class P>
+__device__ __forceinline__ void store_vec(typename P::vec *p, const typename P::C *r) {
+  *p = narrow_vec(r, (typename P::vec *)nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Operator kinds handled by the stencil kernel.
+enum OpKind { OP_DHOP = 0, OP_DHOP_DAG = 1, OP_D = 2, OP_DDAG = 3 };
+
+struct DslashParams {
+  void *out;
+  const void *in;
+  const void *gmain;  // [mu][16/R][V4] vec
+  const void *gtail;  // [mu][V4] tvec
+  int L[4];
+  int V4;
+  int Ls;
+  long long plane;       // vecs per fermion plane (= Ls * V4)
+  long long rhs_stride;  // vecs per right-hand side (= 24/R planes)
+  int nrhs;             // right-hand sides in this launch (<= kMaxRhsPerLaunch)
+  const int *gate;      // optional: CTAs of RHS r run only if gate[r * gate_stride] != 0
+  int gate_stride;
+  double M5, b, c;
+  double mf[64];         // per-RHS masses, passed by value
+};
+
+constexpr int kMaxRhsPerLaunch = 64;
+
+// Launch configuration chosen by the tuner.
+struct TileConfig {
+  int spt;  // fifth-dimension slices per thread
+  int tx;   // 4D sites per CTA (multiple of 32)
+};
+
+int launch_dslash_f64(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int launch_dslash_f32(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int launch_dslash_f16(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+// Largest CTA the stencil kernel (op, spt) can launch with (0 if unknown).
+int dslash_max_threads_f64(int op, int spt);
+int dslash_max_threads_f32(int op, int spt);
+int dslash_max_threads_f16(int op, int spt);
+
+struct CGWork;
+
+}  // namespace dw
+
+// ---------------------------------------------------------------------------
+// The lattice object behind the opaque handle.
+struct dw_lattice {
+  int dims[4];
+  int Ls;
+  long long V4;
+  long long V5;
+  int kind;
+  double M5, b, c;
+  int prec;
+  int bc[4];
+  int device;
+  int num_sms;
+  bool gauge_loaded;
+  // gauge copies per precision: main planes and tail plane
+  void *gmain[3];
+  void *gtail[3];
+  // scratch: one field for D^+D, host-apply staging, reduction partials
+  void *scratch;
+  size_t scratch_bytes;
+  void *stage_in, *stage_out;
+  size_t stage_bytes;
+  double *partials;   // reduction partials
+  size_t partials_cap;
+  // tuning cache: (prec, op, nrhs) -> tile
+  std::map<std::tuple<int, int, int>, dw::TileConfig> tuned;
+  // solver workspace (dw_cg_solve), created on first use
+  dw::CGWork *cg;
+};

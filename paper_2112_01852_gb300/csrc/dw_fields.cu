@@ -1,0 +1,224 @@
+// Field layout kernels: canonical <-> internal fermion packing, gauge
+// conversion with the boundary signs folded in, and precision conversion.
+#include "dw_fields.cuh"
+
+namespace dw {
+
+// ---------------------------------------------------------------------------
+// Canonical fermion complex128 [rhs][x4][s][spin][col] <-> internal planes.
+// One thread per (x4, s) of one RHS; the 24 reals of the site map to the
+// internal reals in the same order (upper spins first).
+template <class P>
+__global__ void pack_kernel(typename P::vec *dst, const double *src, long long V5, int V4,
+                            int Ls, long long plane, long long rhs_stride) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (i >= V5) return;
+  const int x4 = (int)(i / Ls);
+  const int s = (int)(i % Ls);
+  const double *p = src + ((long long)rhs * V5 + i) * 24;
+  typename P::vec *d = dst + (long long)rhs * rhs_stride + (long long)s * V4 + x4;
+  constexpr int NP = 24 / P::R;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    double r[P::R];
+#pragma unroll
+    for (int k = 0; k < P::R; ++k) r[k] = p[q * P::R + k];
+    d[q * plane] = narrow_from_f64(r, (typename P::vec *)nullptr);
+  }
+}
+
+template <class P>
+__global__ void unpack_kernel(double *dst, const typename P::vec *src, long long V5, int V4,
+                              int Ls, long long plane, long long rhs_stride) {
+  using C = typename P::C;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (i >= V5) return;
+  const int x4 = (int)(i / Ls);
+  const int s = (int)(i % Ls);
+  double *p = dst + ((long long)rhs * V5 + i) * 24;
+  const typename P::vec *sp = src + (long long)rhs * rhs_stride + (long long)s * V4 + x4;
+  constexpr int NP = 24 / P::R;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    C r[P::R];
+    load_vec<P>(r, sp + q * plane);
+#pragma unroll
+    for (int k = 0; k < P::R; ++k) p[q * P::R + k] = (double)r[k];
+  }
+}
+
+template <class P>
+static int pack_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cudaStream_t st) {
+  const long long V5 = g.V5();
+  const int tpb = 256;
+  dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
+  const long long plane = (long long)g.Ls * g.V4;
+  pack_kernel<P><<<grid, tpb, 0, st>>>((typename P::vec *)dst, (const double *)src, V5, g.V4,
+                                       g.Ls, plane, plane * (24 / P::R));
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class P>
+static int unpack_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cudaStream_t st) {
+  const long long V5 = g.V5();
+  const int tpb = 256;
+  dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
+  const long long plane = (long long)g.Ls * g.V4;
+  unpack_kernel<P><<<grid, tpb, 0, st>>>((double *)dst, (const typename P::vec *)src, V5, g.V4,
+                                         g.Ls, plane, plane * (24 / P::R));
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int pack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int nrhs,
+                 cudaStream_t st) {
+  switch (prec) {
+    case DW_F64: return pack_t<F64>(g, dst, src, nrhs, st);
+    case DW_F32: return pack_t<F32>(g, dst, src, nrhs, st);
+    case DW_F16: return pack_t<F16>(g, dst, src, nrhs, st);
+  }
+  return -2;
+}
+
+int unpack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int nrhs,
+                   cudaStream_t st) {
+  switch (prec) {
+    case DW_F64: return unpack_t<F64>(g, dst, src, nrhs, st);
+    case DW_F32: return unpack_t<F32>(g, dst, src, nrhs, st);
+    case DW_F16: return unpack_t<F16>(g, dst, src, nrhs, st);
+  }
+  return -2;
+}
+
+// ---------------------------------------------------------------------------
+// Gauge: canonical complex128 [x4][mu][row][col] -> per precision main planes
+// [mu][16/R][V4] + tail plane [mu][V4].  A link U_mu(x) with x_mu = L_mu - 1
+// crosses the lattice edge and is multiplied by bc[mu].
+template <class P>
+__device__ __forceinline__ void store_link(void *gmain, void *gtail, int mu, int x4, int V4,
+                                          const double *u) {
+  constexpr int NM = 16 / P::R;
+  typename P::vec *m = (typename P::vec *)gmain + (long long)mu * NM * V4 + x4;
+#pragma unroll
+  for (int q = 0; q < NM; ++q)
+    m[(long long)q * V4] = narrow_from_f64(u + q * P::R, (typename P::vec *)nullptr);
+  ((typename P::tvec *)gtail)[(long long)mu * V4 + x4] =
+      narrow_t_from_f64(u + 16, (typename P::tvec *)nullptr);
+}
+
+__global__ void gauge_kernel(const double *U, int L0, int L1, int L2, int L3, int bc0, int bc1,
+                             int bc2, int bc3, void *m64, void *t64, void *m32, void *t32,
+                             void *m16, void *t16) {
+  const long long V4 = (long long)L0 * L1 * L2 * L3;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 4 * V4) return;
+  const int x4 = (int)(i / 4);
+  const int mu = (int)(i % 4);
+  int c[4];
+  int rem = x4;
+  c[0] = rem % L0;
+  rem /= L0;
+  c[1] = rem % L1;
+  rem /= L1;
+  c[2] = rem % L2;
+  c[3] = rem / L2;
+  const int L[4] = {L0, L1, L2, L3};
+  const int bc[4] = {bc0, bc1, bc2, bc3};
+  const double f = (c[mu] == L[mu] - 1) ? (double)bc[mu] : 1.0;
+  double u[18];
+  const double *src = U + ((long long)x4 * 4 + mu) * 18;
+#pragma unroll
+  for (int k = 0; k < 18; ++k) u[k] = f * src[k];
+  store_link<F64>(m64, t64, mu, x4, (int)V4, u);
+  store_link<F32>(m32, t32, mu, x4, (int)V4, u);
+  store_link<F16>(m16, t16, mu, x4, (int)V4, u);
+}
+
+int load_gauge(const FieldGeom &g, const int bc[4], const void *U, void *const gmain[3],
+               void *const gtail[3], cudaStream_t st) {
+  const long long n = 4LL * g.V4;
+  const int tpb = 256;
+  gauge_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
+      (const double *)U, g.L[0], g.L[1], g.L[2], g.L[3], bc[0], bc[1], bc[2], bc[3], gmain[0],
+      gtail[0], gmain[1], gtail[1], gmain[2], gtail[2]);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Precision conversion between internal fields: one thread per "quad" (4
+// reals at one 5D site: plane q of F32/F16, planes 2q and 2q+1 of F64).
+template <class P>
+__device__ __forceinline__ void load_quad(typename P::C *r, const void *base, long long q,
+                                          long long i, long long plane) {
+  const typename P::vec *b = (const typename P::vec *)base;
+  if (P::R == 4) {
+    load_vec<P>(r, b + q * plane + i);
+  } else {
+    load_vec<P>(r, b + 2 * q * plane + i);
+    load_vec<P>(r + 2, b + (2 * q + 1) * plane + i);
+  }
+}
+
+template <class P>
+__device__ __forceinline__ void store_quad(void *base, long long q, long long i, long long plane,
+                                           const typename P::C *r) {
+  typename P::vec *b = (typename P::vec *)base;
+  if (P::R == 4) {
+    store_vec<P>(b + q * plane + i, r);
+  } else {
+    store_vec<P>(b + 2 * q * plane + i, r);
+    store_vec<P>(b + (2 * q + 1) * plane + i, r + 2);
+  }
+}
+
+template <class PI, class PO>
+__global__ void convert_kernel(void *dst, const void *src, long long V5, long long rhs_in,
+                               long long rhs_out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (i >= V5) return;
+  const char *s = (const char *)src + rhs * rhs_in;
+  char *d = (char *)dst + rhs * rhs_out;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    typename PI::C a[4];
+    load_quad<PI>(a, s, q, i, V5);
+    typename PO::C b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] = (typename PO::C)a[k];
+    store_quad<PO>(d, q, i, V5, b);
+  }
+}
+
+template <class PI, class PO>
+static int convert_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cudaStream_t st) {
+  const long long V5 = g.V5();
+  const int tpb = 256;
+  dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
+  convert_kernel<PI, PO><<<grid, tpb, 0, st>>>(dst, src, V5, 24 * V5 * PI::RB, 24 * V5 * PO::RB);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class PI>
+static int convert_to(const FieldGeom &g, int po, void *dst, const void *src, int nrhs,
+                      cudaStream_t st) {
+  switch (po) {
+    case DW_F64: return convert_t<PI, F64>(g, dst, src, nrhs, st);
+    case DW_F32: return convert_t<PI, F32>(g, dst, src, nrhs, st);
+    case DW_F16: return convert_t<PI, F16>(g, dst, src, nrhs, st);
+  }
+  return -2;
+}
+
+int convert_fermion(const FieldGeom &g, int pi, int po, void *dst, const void *src, int nrhs,
+                    cudaStream_t st) {
+  switch (pi) {
+    case DW_F64: return convert_to<F64>(g, po, dst, src, nrhs, st);
+    case DW_F32: return convert_to<F32>(g, po, dst, src, nrhs, st);
+    case DW_F16: return convert_to<F16>(g, po, dst, src, nrhs, st);
+  }
+  return -2;
+}
+
+}  // namespace dw

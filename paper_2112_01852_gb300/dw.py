@@ -1,0 +1,218 @@
+"""ctypes binding of libdw_gb300.so with the C ABI's names (include/dw.h).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name, raises DWError on a negative status, and takes device buffers as
+integer pointers (``tensor.data_ptr()``) and streams as integer handles
+(``torch.cuda.current_stream().cuda_stream``).  There is no fallback: if the
+CUDA library has not been built, loading fails loudly.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdw_gb300.so")
+
+DW_OK = 0
+DW_ERR_ARG = -1
+DW_ERR_ALLOC = -2
+DW_ERR_CUDA = -3
+DW_ERR_STATE = -4
+DW_ERR_NOT_CONVERGED = -5
+DW_ERR_BREAKDOWN = -6
+DW_ERR_TIMEOUT = -7
+
+DW_SHAMIR = 0
+DW_MOBIUS = 1
+DW_F64 = 0
+DW_F32 = 1
+DW_F16 = 2
+
+DW_OP_DHOP = 0
+DW_OP_DHOP_DAG = 1
+DW_OP_D = 2
+DW_OP_DDAG = 3
+DW_OP_DDAGD = 4
+
+_ERRNAMES = {
+    DW_ERR_ARG: "DW_ERR_ARG",
+    DW_ERR_ALLOC: "DW_ERR_ALLOC",
+    DW_ERR_CUDA: "DW_ERR_CUDA",
+    DW_ERR_STATE: "DW_ERR_STATE",
+    DW_ERR_NOT_CONVERGED: "DW_ERR_NOT_CONVERGED",
+    DW_ERR_BREAKDOWN: "DW_ERR_BREAKDOWN",
+    DW_ERR_TIMEOUT: "DW_ERR_TIMEOUT",
+}
+
+# Every symbol include/dw.h declares.
+SYMBOLS = (
+    "dw_create_lattice", "dw_destroy_lattice", "dw_load_gauge", "dw_apply_Dhop",
+    "dw_apply_Dhop_dag", "dw_apply_D", "dw_apply_Ddag", "dw_apply_DdagD", "dw_apply_host",
+    "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_fermion_bytes", "dw_pack_fermion",
+    "dw_unpack_fermion", "dw_last_error",
+)
+
+
+class DWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class dw_cg_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("reliable_updates", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("true_resid", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library():
+    """Load the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libdw_gb300.so not found at %s: build it first (paper_2112_01852_gb300.build)"
+                % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        IP = ctypes.POINTER(ctypes.c_int)
+        DP = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "dw_create_lattice": (I, [ctypes.POINTER(P), IP, I, I, D, D, D, I, IP]),
+            "dw_destroy_lattice": (None, [P]),
+            "dw_load_gauge": (I, [P, P, P]),
+            "dw_apply_Dhop": (I, [P, P, P, I, P]),
+            "dw_apply_Dhop_dag": (I, [P, P, P, I, P]),
+            "dw_apply_D": (I, [P, P, P, DP, I, P]),
+            "dw_apply_Ddag": (I, [P, P, P, DP, I, P]),
+            "dw_apply_DdagD": (I, [P, P, P, DP, I, P]),
+            "dw_apply_host": (I, [P, I, P, P, DP, I, P]),
+            "dw_cg_solve": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
+            "dw_set_tile": (I, [P, I, I, I, I, I]),
+            "dw_tune": (I, [P, I, I, IP, IP, P]),
+            "dw_fermion_bytes": (S, [P, I, I]),
+            "dw_pack_fermion": (I, [P, P, I, P, I, P]),
+            "dw_unpack_fermion": (I, [P, P, P, I, I, P]),
+            "dw_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, allow=()):
+    if rc < 0 and rc not in allow:
+        msg = load_library().dw_last_error().decode(errors="replace")
+        raise DWError(rc, msg)
+    return rc
+
+
+def _ints(v, n):
+    if v is None:
+        return None
+    arr = (ctypes.c_int * n)(*[int(x) for x in v])
+    return arr
+
+
+def _doubles(v):
+    if v is None:
+        return None
+    v = [float(x) for x in v]
+    return (ctypes.c_double * len(v))(*v)
+
+
+def dw_last_error() -> str:
+    return load_library().dw_last_error().decode(errors="replace")
+
+
+def dw_create_lattice(dims, Ls, kind, M5, b, c, prec, bc=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.dw_create_lattice(ctypes.byref(h), _ints(dims, 4), int(Ls), int(kind), float(M5),
+                                 float(b), float(c), int(prec), _ints(bc, 4)))
+    return h.value
+
+
+def dw_destroy_lattice(lat):
+    load_library().dw_destroy_lattice(lat)
+
+
+def dw_load_gauge(lat, U, stream=0):
+    _check(load_library().dw_load_gauge(lat, U, stream))
+
+
+def dw_apply_Dhop(lat, out, inp, nrhs, stream=0):
+    _check(load_library().dw_apply_Dhop(lat, out, inp, int(nrhs), stream))
+
+
+def dw_apply_Dhop_dag(lat, out, inp, nrhs, stream=0):
+    _check(load_library().dw_apply_Dhop_dag(lat, out, inp, int(nrhs), stream))
+
+
+def dw_apply_D(lat, out, inp, mf, nrhs, stream=0):
+    _check(load_library().dw_apply_D(lat, out, inp, _doubles(mf), int(nrhs), stream))
+
+
+def dw_apply_Ddag(lat, out, inp, mf, nrhs, stream=0):
+    _check(load_library().dw_apply_Ddag(lat, out, inp, _doubles(mf), int(nrhs), stream))
+
+
+def dw_apply_DdagD(lat, out, inp, mf, nrhs, stream=0):
+    _check(load_library().dw_apply_DdagD(lat, out, inp, _doubles(mf), int(nrhs), stream))
+
+
+def dw_apply_host(lat, op, out_host, in_host, mf, nrhs, stream=0):
+    _check(load_library().dw_apply_host(lat, int(op), out_host, in_host, _doubles(mf), int(nrhs),
+                                        stream))
+
+
+def dw_cg_solve(lat, x, b, mf, nrhs, tol, maxit, mode, stream=0):
+    """Returns (status, [dw_cg_stats]*nrhs); status may be DW_ERR_NOT_CONVERGED."""
+    stats = (dw_cg_stats * int(nrhs))()
+    rc = _check(load_library().dw_cg_solve(lat, x, b, _doubles(mf), int(nrhs), float(tol),
+                                           int(maxit), int(mode), stats, stream),
+                allow=(DW_ERR_NOT_CONVERGED,))
+    return rc, list(stats)
+
+
+def dw_set_tile(lat, op, prec, nrhs, spt, tx):
+    _check(load_library().dw_set_tile(lat, int(op), int(prec), int(nrhs), int(spt), int(tx)))
+
+
+def dw_tune(lat, op, nrhs, stream=0):
+    """Returns the chosen (spt, tx)."""
+    spt = ctypes.c_int()
+    tx = ctypes.c_int()
+    _check(load_library().dw_tune(lat, int(op), int(nrhs), ctypes.byref(spt), ctypes.byref(tx),
+                                  stream))
+    return spt.value, tx.value
+
+
+def dw_fermion_bytes(lat, prec, nrhs):
+    return int(load_library().dw_fermion_bytes(lat, int(prec), int(nrhs)))
+
+
+def dw_pack_fermion(lat, dst_internal, prec, src_c128, nrhs, stream=0):
+    _check(load_library().dw_pack_fermion(lat, dst_internal, int(prec), src_c128, int(nrhs),
+                                          stream))
+
+
+def dw_unpack_fermion(lat, dst_c128, src_internal, prec, nrhs, stream=0):
+    _check(load_library().dw_unpack_fermion(lat, dst_c128, src_internal, int(prec), int(nrhs),
+                                            stream))

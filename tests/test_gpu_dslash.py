@@ -1,0 +1,253 @@
+"""GPU parity of the stencil operators (Dhop, Dhop^+, D, D^+, D^+D) against the
+CPU oracle, through the C ABI, on the same seeded inputs.
+
+Tolerances (relative L2 over each right-hand side): 1e-12 at FP64, 1e-5 at
+FP32 storage, 5e-3 at FP16 storage.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import (ALL_OPS, BC, OP_NAMES, STENCIL_OPS, TOL, build_library, make_case,
+                         max_rel, run_gpu, run_oracle, valid_tiles)
+from paper_2112_01852_gb300 import dw
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_library()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def _lattice(dims, Ls, kind, prec, M5=1.8, b=1.5, c=0.5, bc=BC):
+    from paper_2112_01852_gb300.lattice import Lattice
+    return Lattice(dims, Ls, kind=kind, M5=M5, b=b, c=c, prec=prec, bc=bc)
+
+
+# ---------------------------------------------------------------------------
+# Shamir D_dw at FP64 on 4^4 x Ls=8, Haar links, seed 1, mf = 0.01
+
+
+@pytest.mark.parametrize("op", ALL_OPS, ids=lambda o: OP_NAMES[o])
+def test_shamir_4x4x4x4_ls8_f64(op):
+    dims, Ls = (4, 4, 4, 4), 8
+    U, psi = make_case(dims, Ls, 1, seed=1, links="haar")
+    lat = _lattice(dims, Ls, dw.DW_SHAMIR, dw.DW_F64)
+    lat.load_gauge(U)
+    got = run_gpu(lat, op, psi, mf=[0.01])
+    ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.0, 0.0, [0.01])
+    assert max_rel(got, ref) <= TOL[dw.DW_F64]
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# Moebius (b=1.5, c=0.5) on 16^4 x Ls=16, exp(i 0.3 H) links, seed 2, FP64/FP32
+
+
+@pytest.fixture(scope="module")
+def case_16x4_ls16():
+    dims, Ls = (16, 16, 16, 16), 16
+    U, psi = make_case(dims, Ls, 1, seed=2)
+    refs = {op: run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01]) for op in ALL_OPS}
+    return dims, Ls, U, psi, refs
+
+
+@pytest.mark.parametrize("prec", [dw.DW_F64, dw.DW_F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("op", ALL_OPS, ids=lambda o: OP_NAMES[o])
+def test_mobius_16x4_ls16(case_16x4_ls16, prec, op):
+    dims, Ls, U, psi, refs = case_16x4_ls16
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
+    lat.load_gauge(U)
+    got = run_gpu(lat, op, psi, mf=[0.01])
+    assert max_rel(got, refs[op]) <= TOL[prec]
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# Every tile on a ragged lattice (V4 = 210 is not a multiple of any tile),
+# including Ls = 1 (the Wilson hop) and Ls = 12 (not a divisor of the warp).
+
+
+@pytest.mark.parametrize("Ls", [1, 6, 12])
+def test_all_tiles_ragged(Ls):
+    dims = (3, 5, 2, 7)
+    bc = (-1, 1, 1, -1)
+    U, psi = make_case(dims, Ls, 2, seed=7)
+    mfs = [0.02, 0.3]
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F64, M5=1.6, b=1.25, c=0.75, bc=bc)
+    lat.load_gauge(U)
+    refs = {op: run_oracle(op, psi, U, dims, Ls, 1.6, 1.25, 0.75, mfs, bc) for op in STENCIL_OPS}
+    ran = 0
+    for spt, tx in valid_tiles(Ls):
+        for op in STENCIL_OPS:
+            try:
+                lat.set_tile(op, spt, tx)
+            except dw.DWError as e:  # CTA beyond this kernel's register budget
+                assert e.code == dw.DW_ERR_ARG
+                continue
+            ran += 1
+            got = run_gpu(lat, op, psi, mf=mfs)
+            err = max_rel(got, refs[op])
+            assert err <= TOL[dw.DW_F64], (OP_NAMES[op], spt, tx, err)
+    assert ran >= len(STENCIL_OPS) * len([t for t in valid_tiles(Ls) if t[1] == 32])
+    lat.close()
+
+
+def test_two_site_lattice_sums_coinciding_neighbours():
+    # On a 2^4 lattice x+mu and x-mu are the same site: both hops must add.
+    dims, Ls = (2, 2, 2, 2), 4
+    U, psi = make_case(dims, Ls, 1, seed=8, links="haar")
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F64)
+    lat.load_gauge(U)
+    for op in ALL_OPS:
+        got = run_gpu(lat, op, psi, mf=[0.05])
+        ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.05])
+        assert max_rel(got, ref) <= TOL[dw.DW_F64], OP_NAMES[op]
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# FP16 storage with FP32 arithmetic
+
+
+@pytest.mark.parametrize("op", ALL_OPS, ids=lambda o: OP_NAMES[o])
+def test_f16_storage(op):
+    dims, Ls = (8, 8, 8, 8), 8
+    U, psi = make_case(dims, Ls, 1, seed=9)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F16)
+    lat.load_gauge(U)
+    got = run_gpu(lat, op, psi, mf=[0.01])
+    ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
+    assert max_rel(got, ref) <= TOL[dw.DW_F16]
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# Several right-hand sides with uneven mass counts (5/4/2/1 over 4 masses)
+
+
+def test_multi_rhs_uneven_masses_f32():
+    dims, Ls = (4, 4, 4, 8), 12
+    mfs = [0.005] * 5 + [0.01] * 4 + [0.02] * 2 + [0.05]
+    U, psi = make_case(dims, Ls, len(mfs), seed=4)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
+    lat.load_gauge(U)
+    for op in ALL_OPS:
+        got = run_gpu(lat, op, psi, mf=mfs)
+        ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mfs)
+        assert max_rel(got, ref) <= TOL[dw.DW_F32], OP_NAMES[op]
+    lat.close()
+
+
+def test_more_rhs_than_one_launch():
+    # 70 RHS are split into launches of at most 64
+    dims, Ls = (2, 2, 2, 4), 2
+    nrhs = 70
+    mfs = list(np.linspace(0.01, 0.7, nrhs))
+    U, psi = make_case(dims, Ls, nrhs, seed=10)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F64)
+    lat.load_gauge(U)
+    for op in (dw.DW_OP_DHOP, dw.DW_OP_D, dw.DW_OP_DDAG):
+        got = run_gpu(lat, op, psi, mf=mfs)
+        ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mfs)
+        assert max_rel(got, ref) <= TOL[dw.DW_F64], OP_NAMES[op]
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# Layout round trips, host-buffer path, tuner, argument errors
+
+
+def test_pack_unpack_roundtrip():
+    dims, Ls = (4, 2, 6, 2), 3
+    _, psi = make_case(dims, Ls, 2, seed=11)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F64)
+    for prec in (dw.DW_F64, dw.DW_F32, dw.DW_F16):
+        back = lat.unpack(lat.pack(psi, prec), 2, prec)
+        if prec == dw.DW_F64:
+            assert np.array_equal(back, psi)
+        elif prec == dw.DW_F32:
+            assert np.array_equal(back.real, psi.real.astype(np.float32).astype(np.float64))
+            assert np.array_equal(back.imag, psi.imag.astype(np.float32).astype(np.float64))
+        else:
+            assert np.array_equal(back.real, psi.real.astype(np.float16).astype(np.float64))
+            assert np.array_equal(back.imag, psi.imag.astype(np.float16).astype(np.float64))
+    lat.close()
+
+
+def test_apply_host_matches_device():
+    import torch
+    dims, Ls = (8, 4, 4, 8), 8
+    U, psi = make_case(dims, Ls, 2, seed=12)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
+    lat.load_gauge(U)
+    x = lat.pack(psi)
+    for op in ALL_OPS:
+        dev = run_gpu(lat, op, psi, mf=[0.01, 0.02])
+        hin = x.cpu().pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        lat.apply_host(op, hout, hin, mf=None if op < dw.DW_OP_D else [0.01, 0.02], nrhs=2)
+        host = lat.unpack(hout.cuda(), 2)
+        assert np.array_equal(host, dev), OP_NAMES[op]
+    lat.close()
+
+
+def test_tune_picks_valid_tile_and_stays_exact():
+    dims, Ls = (8, 8, 8, 8), 12
+    U, psi = make_case(dims, Ls, 1, seed=13)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
+    lat.load_gauge(U)
+    for op in STENCIL_OPS:
+        spt, tx = lat.tune(op, 1)
+        assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
+        got = run_gpu(lat, op, psi, mf=[0.01])
+        ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
+        assert max_rel(got, ref) <= TOL[dw.DW_F32], OP_NAMES[op]
+    lat.close()
+
+
+def test_argument_errors():
+    import torch
+    dims, Ls = (4, 4, 4, 4), 4
+    with pytest.raises(dw.DWError) as e:
+        dw.dw_create_lattice((4, 0, 4, 4), 4, dw.DW_MOBIUS, 1.8, 1.5, 0.5, dw.DW_F32)
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        dw.dw_create_lattice(dims, 0, dw.DW_MOBIUS, 1.8, 1.5, 0.5, dw.DW_F32)
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        dw.dw_create_lattice(dims, 4, dw.DW_MOBIUS, 1.8, 1.5, 0.5, 7)
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        dw.dw_create_lattice(dims, 4, dw.DW_MOBIUS, 1.8, 1.5, 0.5, dw.DW_F32, bc=(1, 1, 2, -1))
+    assert e.value.code == dw.DW_ERR_ARG
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
+    x = lat.empty(1)
+    y = lat.empty(1)
+    with pytest.raises(dw.DWError) as e:  # gauge not loaded yet
+        lat.dhop(y, x)
+    assert e.value.code == dw.DW_ERR_STATE
+    U, _ = make_case(dims, Ls, 1, seed=14)
+    lat.load_gauge(U)
+    with pytest.raises(dw.DWError) as e:  # aliasing
+        lat.dhop(x, x)
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:  # misaligned
+        dw.dw_apply_Dhop(lat.handle, y.data_ptr() + 4, x.data_ptr(), 1)
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:  # null mass array
+        dw.dw_apply_D(lat.handle, y.data_ptr(), x.data_ptr(), None, 1)
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        lat.set_tile(dw.DW_OP_DHOP, 3, 32)  # 3 does not divide Ls = 4
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        lat.set_tile(dw.DW_OP_DHOP, 1, 48)  # not a multiple of 32
+    assert e.value.code == dw.DW_ERR_ARG
+    assert "multiple" in dw.dw_last_error() or "invalid" in dw.dw_last_error()
+    torch.cuda.synchronize()
+    lat.close()
