@@ -128,13 +128,22 @@ def _barrier(ws):
 
 
 def _max_over_ranks(ws, v):
+    """Max of a host scalar over the ranks (NCCL: via a CUDA tensor; gloo: CPU)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as tdist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ws, ms_local, units_local):
+    """Whole-job figure of N independent replicas: every rank processes
+    units_local units in ms_local; the job takes the slowest rank's time."""
+    ms = _max_over_ranks(ws, ms_local)
+    return ms, units_local * ws / (ms * 1e-3)
 
 
 def time_op(fn, steps, warmup, stream):
@@ -210,8 +219,103 @@ def run_reference(args):
     return 0
 
 
+CG_DIMS, CG_LS, CG_SEED = (24, 24, 24, 24), 16, 3
+BATCH_DIMS, BATCH_LS, BATCH_SEED = (16, 16, 16, 32), 12, 4
+BATCH_MASSES = [0.005] * 5 + [0.01] * 4 + [0.02] * 2 + [0.05]
+
+
+def bench_cg(args):
+    """CG on D^+D x = b to a true residual of 1e-10 at 24^4 x Ls=16, m_f = 0.01:
+    plain FP64 against mixed FP32 and mixed FP16-storage, wall time of the whole
+    dw_cg_solve call; every solution's residual is recomputed by the oracle."""
+    import oracle
+    import torch
+    from paper_2112_01852_gb300 import dw, inputs
+    from paper_2112_01852_gb300.lattice import Lattice
+    U = inputs.exp_su3_field(CG_DIMS, seed=CG_SEED)
+    rhs = inputs.gaussian_fermion(CG_DIMS, CG_LS, 1, seed=CG_SEED)
+    lat = Lattice(CG_DIMS, CG_LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
+    lat.load_gauge(U)
+    bdev = lat.pack(rhs)
+    out = {"workload": "mobius_cg_24x24x24x24_ls16_mf0.01", "tol": 1e-10}
+    for name, mode in (("f64", dw.DW_F64), ("mixed_f32", dw.DW_F32), ("mixed_f16", dw.DW_F16)):
+        x = lat.empty(1)
+        torch.cuda.synchronize()
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status, stats = lat.cg(x, bdev, [MF], nrhs=1, tol=1e-10, maxit=40000, mode=mode)
+        wall = time.perf_counter() - t0
+        xs = lat.unpack(x)
+        Ax = oracle.dwdagdw(xs, U, CG_DIMS, CG_LS, M5, B, C, [MF])
+        res = float(np.linalg.norm((rhs - Ax).ravel()) / np.linalg.norm(rhs.ravel()))
+        out[name] = {"seconds": wall, "status": status, "iters": stats[0].iters,
+                     "reliable_updates": stats[0].reliable_updates,
+                     "converged": stats[0].converged, "true_resid": stats[0].true_resid,
+                     "oracle_resid": res}
+        del x
+    out["speedup_mixed_f32"] = out["f64"]["seconds"] / out["mixed_f32"]["seconds"]
+    out["speedup_mixed_f16"] = out["f64"]["seconds"] / out["mixed_f16"]["seconds"]
+    lat.close()
+    return out
+
+
+def bench_batched(args):
+    """12 right-hand sides over 4 masses (5/4/2/1) at 16^3 x 32 x Ls=12, FP32:
+    one batched Dhop / D^+D launch per step, and one batched mixed-FP32 CG solve
+    of all 12 systems (residuals recomputed by the oracle)."""
+    import oracle
+    import torch
+    from paper_2112_01852_gb300 import dw, inputs
+    from paper_2112_01852_gb300.lattice import Lattice
+    nrhs = len(BATCH_MASSES)
+    U = inputs.exp_su3_field(BATCH_DIMS, seed=BATCH_SEED)
+    rhs = inputs.gaussian_fermion(BATCH_DIMS, BATCH_LS, nrhs, seed=BATCH_SEED)
+    V5 = int(np.prod(BATCH_DIMS)) * BATCH_LS
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    lat = Lattice(BATCH_DIMS, BATCH_LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32)
+    lat.load_gauge(U)
+    x = lat.pack(rhs)
+    y = lat.empty(nrhs)
+    tile = lat.tune(dw.DW_OP_DHOP, nrhs)
+    ms = time_op(lambda: dw.dw_apply_Dhop(lat.handle, y.data_ptr(), x.data_ptr(), nrhs, sh),
+                 max(5, args.steps // 2), 3, stream)
+    bps = bytes_per_site(4, BATCH_LS, nrhs)
+    out = {"workload": "mobius_batched_16x16x16x32_ls12_12rhs_f32", "nrhs": nrhs,
+           "masses": BATCH_MASSES, "dhop": {"ms": ms, "gflops": FLOP_DHOP * V5 * nrhs / ms / 1e6,
+                                            "gbs": bps * V5 * nrhs / ms / 1e6, "tile": tile}}
+    ms2 = time_op(lambda: dw.dw_apply_DdagD(lat.handle, y.data_ptr(), x.data_ptr(),
+                                            BATCH_MASSES, nrhs, sh), max(5, args.steps // 4), 3,
+                  stream)
+    out["ddagd"] = {"ms": ms2, "gflops": 2 * FLOP_D_MOBIUS * V5 * nrhs / ms2 / 1e6}
+    lat.close()
+    del x, y
+    lat = Lattice(BATCH_DIMS, BATCH_LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
+    lat.load_gauge(U)
+    bdev = lat.pack(rhs)
+    xs = lat.empty(nrhs)
+    xs.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status, stats = lat.cg(xs, bdev, BATCH_MASSES, nrhs=nrhs, tol=1e-10, maxit=40000,
+                           mode=dw.DW_F32)
+    wall = time.perf_counter() - t0
+    sol = lat.unpack(xs, nrhs)
+    Ax = oracle.dwdagdw(sol, U, BATCH_DIMS, BATCH_LS, M5, B, C, BATCH_MASSES)
+    res = [float(np.linalg.norm((rhs[r] - Ax[r]).ravel()) / np.linalg.norm(rhs[r].ravel()))
+           for r in range(nrhs)]
+    out["cg_mixed_f32"] = {"seconds": wall, "status": status,
+                           "iters": [s.iters for s in stats],
+                           "reliable_updates": [s.reliable_updates for s in stats],
+                           "max_oracle_resid": max(res)}
+    lat.close()
+    return out
+
+
 def _config():
-    return {"workload": "mobius_dwf_dhop_32x32x32x64_ls12_f32", "dims": list(DIMS), "Ls": LS,
+    name = "mobius_dwf_dhop_%s_ls%d_f32" % ("x".join(str(d) for d in DIMS), LS)
+    return {"workload": name, "dims": list(DIMS), "Ls": LS,
             "nrhs": 1, "kind": "mobius", "M5": M5, "b": B, "c": C, "mf": MF,
             "links": "exp(i 0.3 H)", "seed": SEED, "prec": "f32",
             "l2": "inputs larger than L2 (2.42 GB FP32 field vs 129 MB L2)"}
@@ -224,7 +328,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dims", default=None,
+                    help="Lx,Ly,Lz,Lt override (profiling runs on a smaller lattice)")
+    ap.add_argument("--Ls", type=int, default=None)
+    ap.add_argument("--main-only", action="store_true",
+                    help="time only the FP32 Dhop (no other operators, e2e, CG or CPU leg)")
+    ap.add_argument("--tile", default=None,
+                    help="spt,tx[,variant]: fixed Dhop tile instead of tuning")
+    ap.add_argument("--no-cg", action="store_true")
     args = ap.parse_args()
+    global DIMS, LS
+    if args.dims:
+        DIMS = tuple(int(v) for v in args.dims.split(","))
+    if args.Ls:
+        LS = args.Ls
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -254,8 +371,16 @@ def main():
     x = lat.pack(psi)
     y = lat.empty(1)
     tiles = {}
-    for op in (dw.DW_OP_DHOP, dw.DW_OP_D, dw.DW_OP_DDAG):
-        tiles[op] = lat.tune(op, 1)
+    if args.tile:
+        tv = [int(v) for v in args.tile.split(",")]
+        spt, tx, var = tv[0], tv[1], (tv[2] if len(tv) > 2 else 0)
+        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var)
+        tiles[dw.DW_OP_DHOP] = (spt, tx, var)
+    else:
+        tiles[dw.DW_OP_DHOP] = lat.tune(dw.DW_OP_DHOP, 1)
+    if not args.main_only:
+        for op in (dw.DW_OP_D, dw.DW_OP_DDAG):
+            tiles[op] = lat.tune(op, 1)
 
     def dhop():
         dw.dw_apply_Dhop(lat.handle, y.data_ptr(), x.data_ptr(), 1, sh)
@@ -278,15 +403,33 @@ def main():
     torch.cuda.synchronize()
     _barrier(ws)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    ms = _max_over_ranks(ws, ms)
-    gflops = FLOP_DHOP * V5 / (ms * 1e-3) / 1e9 * ws
+    ms, sites_per_s = aggregate(ws, e0.elapsed_time(e1) / args.steps, V5)
+    gflops = FLOP_DHOP * sites_per_s / 1e9
 
     # roofline of the Dhop kernel (one launch per step)
     peak, peak_kind = _peaks()
     bps = bytes_per_site(4, LS)
     alg_bytes = bps * V5
     achieved = alg_bytes / (ms * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": gflops, "unit": "GFlop/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": _config(),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind,
+                     "bytes_per_site": bps, "sites_per_launch": V5},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "tile": tiles[dw.DW_OP_DHOP],
+    }
+    if args.main_only:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        lat.close()
+        return 0
 
     # other operators on the same lattice (kernel-only, same event method)
     mf = [MF]
@@ -306,8 +449,8 @@ def main():
                  "gbs": alg_bytes / ops["Ddag"] / 1e6},
         "DdagD": {"ms": ops["DdagD"], "gflops": 2 * FLOP_D_MOBIUS * V5 / ops["DdagD"] / 1e6,
                   "gbs": 2 * alg_bytes / ops["DdagD"] / 1e6},
-        "tiles": {"Dhop": tiles[dw.DW_OP_DHOP], "D": tiles[dw.DW_OP_D],
-                  "Ddag": tiles[dw.DW_OP_DDAG]},
+        "tiles": {"Dhop": tiles[dw.DW_OP_DHOP], "D": tiles.get(dw.DW_OP_D),
+                  "Ddag": tiles.get(dw.DW_OP_DDAG)},
     }
     # FP16-storage Dhop on the same lattice
     lat16 = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F16)
@@ -333,31 +476,23 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         lat.apply_host(dw.DW_OP_DHOP, hout, hin)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_s = _max_over_ranks(ws, e2e_s)
-    e2e = {"value": FLOP_DHOP * V5 / e2e_s / 1e9 * ws, "unit": "GFlop/s",
+    e2e_ms, e2e_rate = aggregate(ws, (time.perf_counter() - t0) / e2e_steps * 1e3, V5)
+    e2e_s = e2e_ms * 1e-3
+    e2e = {"value": FLOP_DHOP * e2e_rate / 1e9, "unit": "GFlop/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
            "ms_per_step": e2e_s * 1e3}
 
-    line = {
-        "metric": METRIC, "value": gflops, "unit": "GFlop/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": _config(),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": peak_kind,
-                     "bytes_per_site": bps, "sites_per_launch": V5},
-        "e2e": e2e,
-        "gpu_launches": args.steps,
-        "clocks": clocks,
-        "ops": ops_out,
-    }
+    line["e2e"] = e2e
+    line["ops"] = ops_out
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(psi, U)
+    del x, y
+    lat.close()
+    if not args.no_cg:
+        line["batched"] = bench_batched(args)
+        line["cg"] = bench_cg(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    lat.close()
     if ws > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()

@@ -34,9 +34,10 @@
  *
  * Internal fermion layout (per RHS): planes [p][s][x4] of 16-byte vectors
  * (8-byte for DW_F16), x4 = x + Lx*(y + Ly*(z + Lz*t)).  The 24 reals of a 5D
- * site are its 4 spins x 3 colours x (re, im) in canonical order; plane p holds
- * reals [p*R, p*R + R) with R = 2 (F64) or 4 (F32, F16).  Planes 0 .. 12/R-1 are
- * the upper (P+) spins, the rest the lower (P-) spins.
+ * site are ordered I = half*12 + c*4 + ri*2 + j (chirality half: 0 = spins 0,1
+ * (P+), 1 = spins 2,3 (P-); colour c; re/im ri; spin j within the half), so
+ * each run of 4 reals is the spin pair (Re, Re, Im, Im) of one colour; plane p
+ * holds reals [p*R, p*R + R) with R = 2 (F64) or 4 (F32, F16).
  *
  * Canonical layout (dw_pack_fermion / dw_unpack_fermion / dw_load_gauge):
  *   fermion complex128 [rhs][x4][s][spin 4][colour 3]
@@ -151,9 +152,13 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
                 double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
 
 /*
- * Stencil-kernel tiles.  A tile is (spt, tx): spt fifth-dimension slices per
- * thread (1..4, dividing Ls) and tx 4D sites per CTA (a multiple of 32); a CTA
- * holds all Ls/spt slice groups of its tx sites.
+ * Stencil-kernel tiles.  A tile is (spt, tx, variant): spt fifth-dimension
+ * slices per thread (1..4, dividing Ls), tx 4D sites per CTA (a multiple of
+ * 32) and the load variant of the hop phase: 0 = neighbour spinors and links
+ * loaded straight into registers, direction by direction; 1 = copied one
+ * direction ahead into shared memory with cp.async; 2, 3 = loaded one
+ * (direction, slice) step ahead into registers, visiting t,z,y,x (2) or
+ * x,y,z,t (3).  A CTA holds all Ls/spt slice groups of its tx sites.
  *
  * dw_set_tile pins the tile used for operator `op` (DW_OP_DHOP .. DW_OP_DDAG)
  * at precision `prec` for launches of `nrhs` right-hand sides (0 = any count
@@ -161,12 +166,12 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
  *
  * dw_tune times every valid tile for (op, nrhs) at the lattice precision on
  * lattice-owned scratch fields (CUDA events on `stream`, median of a few
- * launches), keeps the fastest for later calls and returns it in *spt, *tx
- * (either may be NULL).  Requires a loaded gauge field; synchronises; must not
+ * launches), keeps the fastest for later calls and returns it in *spt, *tx,
+ * *variant (any may be NULL).  Requires a loaded gauge field; synchronises; must not
  * be called while `stream` is being captured into a graph.
  */
-int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx);
-int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, void *stream);
+int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant);
+int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, void *stream);
 
 /* Bytes of one internal-layout field of nrhs right-hand sides at precision prec. */
 size_t dw_fermion_bytes(const dw_lattice *lat, int prec, int nrhs);

@@ -59,25 +59,16 @@ int ensure_buffer(void **buf, size_t *cap, size_t need) {
   return DW_OK;
 }
 
-int dslash_max_threads(int prec, int op, int spt) {
-  switch (prec) {
-    case DW_F64: return dslash_max_threads_f64(op, spt);
-    case DW_F32: return dslash_max_threads_f32(op, spt);
-    case DW_F16: return dslash_max_threads_f16(op, spt);
-  }
-  return 0;
-}
-
 // Untuned choice: the smallest slices-per-thread whose CTA of 32 sites x Ls/spt
 // slice groups fits the kernel's register budget, then up to 256 threads.
 TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs) {
   (void)nrhs;
   const int Ls = lat->Ls;
-  TileConfig t{0, 32};
+  TileConfig t{0, 32, 0};
   int maxt = 0;
   for (int spt : {1, 2, 3, 4}) {
     if (Ls % spt) continue;
-    const int m = dslash_max_threads(prec, op, spt);
+    const int m = dslash_max_threads(prec, op, spt, 0);
     if ((Ls / spt) * 32 <= m) {
       t.spt = spt;
       maxt = m;
@@ -104,8 +95,9 @@ TileConfig pick_tile(dw_lattice *lat, int prec, int op, int nrhs) {
 bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (t.spt < 1 || t.spt > 4 || lat->Ls % t.spt) return false;
   if (t.tx < 32 || t.tx % 32) return false;
+  if (t.variant < 0 || t.variant > kNumVariants - 1) return false;
   const long long threads = (long long)t.tx * (lat->Ls / t.spt);
-  return threads <= 1024 && threads <= dslash_max_threads(prec, op, t.spt);
+  return threads <= 1024 && threads <= dslash_max_threads(prec, op, t.spt, t.variant);
 }
 
 // Stencil launch over all RHS, in groups of at most kMaxRhsPerLaunch.
@@ -134,18 +126,14 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.c = lat->c;
     for (int r = 0; r < n; ++r) p.mf[r] = mf_host ? mf_host[r0 + r] : 0.0;
     const TileConfig cfg = force ? *force : pick_tile(lat, prec, op, nrhs);
-    int rc;
-    switch (prec) {
-      case DW_F64: rc = launch_dslash_f64(p, op, cfg, st); break;
-      case DW_F32: rc = launch_dslash_f32(p, op, cfg, st); break;
-      case DW_F16: rc = launch_dslash_f16(p, op, cfg, st); break;
-      default: rc = -2;
-    }
-    if (rc == -2) return fail(DW_ERR_ARG, "unsupported tile (spt=%d, tx=%d) for Ls=%d", cfg.spt,
-                              cfg.tx, lat->Ls);
+    const int rc = launch_dslash(p, prec, op, cfg, st);
+    if (rc == -2)
+      return fail(DW_ERR_ARG, "unsupported tile (spt=%d, tx=%d, variant=%d) for Ls=%d", cfg.spt,
+                  cfg.tx, cfg.variant, lat->Ls);
     if (rc == -3)
-      return fail(DW_ERR_ARG, "tile (spt=%d, tx=%d) exceeds the kernel's threads per CTA",
-                  cfg.spt, cfg.tx);
+      return fail(DW_ERR_ARG,
+                  "tile (spt=%d, tx=%d, variant=%d) exceeds the kernel's CTA limits", cfg.spt,
+                  cfg.tx, cfg.variant);
     if (rc) return cuda_fail(cudaGetLastError(), "dslash launch");
   }
   return DW_OK;
@@ -341,21 +329,23 @@ int dw_apply_host(dw_lattice *lat, int op, void *out_host, const void *in_host, 
   return DW_OK;
 }
 
-int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx) {
+int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant) {
   clear_error();
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
   if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
   if (prec < DW_F64 || prec > DW_F16) return fail(DW_ERR_ARG, "unknown precision %d", prec);
   if (nrhs < 0) return fail(DW_ERR_ARG, "nrhs must be >= 0");
-  TileConfig t{spt, tx};
+  TileConfig t{spt, tx, variant};
   if (!tile_valid(lat, prec, op, t))
-    return fail(DW_ERR_ARG, "invalid tile spt=%d tx=%d for Ls=%d (slices per thread must divide Ls, "
-                "tx a multiple of 32, CTA within the kernel's thread limit)", spt, tx, lat->Ls);
+    return fail(DW_ERR_ARG,
+                "invalid tile spt=%d tx=%d variant=%d for Ls=%d (slices per thread must divide "
+                "Ls, tx a multiple of 32, variant 0..3, CTA within the kernel's limits)",
+                spt, tx, variant, lat->Ls);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;
   return DW_OK;
 }
 
-int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, void *stream) {
+int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, void *stream) {
   clear_error();
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
   if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
@@ -370,6 +360,7 @@ int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, void *stream) 
   const TileConfig t = pick_tile(lat, lat->prec, op, nrhs);
   if (spt) *spt = t.spt;
   if (tx) *tx = t.tx;
+  if (variant) *variant = t.variant;
   return DW_OK;
 }
 

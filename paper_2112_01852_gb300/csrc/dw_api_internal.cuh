@@ -15,7 +15,6 @@ int ensure_buffer(void **buf, size_t *cap, size_t need);
 TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs);
 TileConfig pick_tile(dw_lattice *lat, int prec, int op, int nrhs);
 bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t);
-int dslash_max_threads(int prec, int op, int spt);
 // Time all valid tiles for (op, nrhs) at the lattice precision; store the best.
 int tune_tile(dw_lattice *lat, int op, int nrhs, cudaStream_t st);
 // Stencil launch (op = OpKind) at precision `prec` over nrhs RHS; mf_host may be

@@ -1,13 +1,272 @@
-// Conjugate gradient on D^+D (plain FP64 and mixed precision).
+// Batched conjugate gradient on D^+D x = b: plain FP64, or mixed precision with
+// reliable updates (the inner operator at FP32 or FP16 storage with FP32
+// arithmetic; FP64 true residuals, reductions and convergence test).
+//
+// The paper gives no solver; this follows textbook CG (Hestenes-Stiefel) for
+// the FP64 mode and CG with reliable updates (Clark et al., "Solving lattice
+// QCD systems of equations using mixed precision solvers on GPUs", 2010) for
+// the mixed modes.  Between reliable updates the inner solver works on the
+// rescaled system A e = r / sigma with sigma = |r| / sqrt(n) (n reals per
+// RHS), so low-precision vectors hold entries of order one; x accumulates
+// x += sigma * e at each update.  A reliable update fires when the iterated
+// residual dropped below delta = 0.1 times its largest value since the last
+// update, when it claims convergence, or when maxit is reached; the FP64
+// residual b - D^+D x then decides convergence.
+//
+// All per-RHS scalars live on the device (CGState); converged or stopped RHS
+// are masked off, and the stencil kernels skip their CTAs.  One inner
+// iteration is captured as a CUDA graph and replayed kReplay times between
+// host checks of the flags.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "dw_api_internal.cuh"
+#include "dw_blas.cuh"
 
 namespace dw {
-void cg_release(dw_lattice *lat) { (void)lat; }
+
+struct CGWork {
+  // FP64 fields (nrhs each)
+  void *r64 = nullptr, *Ax64 = nullptr, *tmp64 = nullptr;
+  size_t r64_cap = 0, Ax64_cap = 0, tmp64_cap = 0;
+  // inner fields
+  void *p = nullptr, *Ap = nullptr, *tmp = nullptr, *rs = nullptr, *xs = nullptr;
+  size_t p_cap = 0, Ap_cap = 0, tmp_cap = 0, rs_cap = 0, xs_cap = 0;
+  double *partials = nullptr;
+  size_t partials_cap = 0;
+  double *sums = nullptr;
+  size_t sums_cap = 0;
+  CGState *state = nullptr;
+  size_t state_cap = 0;
+  cudaStream_t stream = nullptr;
+};
+
+void cg_release(dw_lattice *lat) {
+  CGWork *w = lat->cg;
+  if (!w) return;
+  void *bufs[] = {w->r64, w->Ax64, w->tmp64, w->p, w->Ap, w->tmp, w->rs, w->xs,
+                  w->partials, w->sums, w->state};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (w->stream) cudaStreamDestroy(w->stream);
+  delete w;
+  lat->cg = nullptr;
+}
+
+namespace {
+
+constexpr int kReplay = 8;  // inner iterations per host check
+
+struct Solve {
+  dw_lattice *lat;
+  CGWork *w;
+  int nrhs;
+  int pp, pr;  // precisions of (p, Ap, tmp) and (r_s, x_s)
+  double delta, tol;
+  int maxit;
+  const double *mf;
+  cudaStream_t st;
+  BlasCtx c;
+
+  const int *gate_run() const { return &w->state[0].run; }
+  const int *gate_update() const { return &w->state[0].need_update; }
+
+  // One inner iteration over all RHS (masked by `run`).
+  int iteration() {
+    int rc = run_dslash(lat, pp, OP_D, w->tmp, w->p, mf, nrhs, st, nullptr, gate_run(),
+                        kCGStateInts);
+    if (rc) return rc;
+    rc = run_dslash(lat, pp, OP_DDAG, w->Ap, w->tmp, mf, nrhs, st, nullptr, gate_run(),
+                    kCGStateInts);
+    if (rc) return rc;
+    if (blas_redot(c, pp, w->p, pp, w->Ap, w->partials, w->state, st) ||
+        cg_alpha(c, w->partials, w->state, st) ||
+        cg_update(c, pp, pr, w->xs, w->rs, w->p, w->Ap, w->partials, w->state, st) ||
+        cg_beta(c, w->partials, w->state, delta, tol, maxit, st) ||
+        cg_direction(c, pp, pr, w->p, w->rs, w->state, st))
+      return cuda_fail(cudaGetLastError(), "cg iteration launch");
+    return DW_OK;
+  }
+
+  // Reliable update of every RHS flagged need_update (first: initial residual).
+  int reliable(void *x, const void *b, int first) {
+    if (!first && cg_accumulate_x(c, pr, x, w->xs, w->state, st))
+      return cuda_fail(cudaGetLastError(), "accumulate launch");
+    int rc = run_dslash(lat, DW_F64, OP_D, w->tmp64, x, mf, nrhs, st, nullptr, gate_update(),
+                        kCGStateInts);
+    if (rc) return rc;
+    rc = run_dslash(lat, DW_F64, OP_DDAG, w->Ax64, w->tmp64, mf, nrhs, st, nullptr,
+                    gate_update(), kCGStateInts);
+    if (rc) return rc;
+    if (cg_residual(c, (double *)w->r64, (const double *)b, (const double *)w->Ax64,
+                    w->partials, w->state, st) ||
+        cg_reliable(c, w->partials, w->state, tol, maxit, first, st) ||
+        cg_install(c, w->state, st) ||
+        cg_reliable_apply(c, pp, pr, (const double *)w->r64, w->rs, w->xs, w->p, w->state, st) ||
+        cg_clear_update(c, w->state, st))
+      return cuda_fail(cudaGetLastError(), "reliable update launch");
+    return DW_OK;
+  }
+};
+
+int ensure(void **buf, size_t *cap, size_t need) { return ensure_buffer(buf, cap, need); }
+
+}  // namespace
+
 }  // namespace dw
+
+using namespace dw;
 
 extern "C" int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs,
                            double tol, int maxit, int mode, dw_cg_stats *stats, void *stream) {
-  (void)lat; (void)x; (void)b; (void)mf; (void)nrhs; (void)tol; (void)maxit; (void)mode;
-  (void)stats; (void)stream;
-  return dw::fail(DW_ERR_STATE, "dw_cg_solve: not available yet");
+  clear_error();
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!x || !b) return fail(DW_ERR_ARG, "field pointer is NULL");
+  if (x == b) return fail(DW_ERR_ARG, "x must not alias b");
+  if (((uintptr_t)x & 15u) || ((uintptr_t)b & 15u))
+    return fail(DW_ERR_ARG, "fields must be 16-byte aligned");
+  if (!mf) return fail(DW_ERR_ARG, "mf is NULL");
+  if (!stats) return fail(DW_ERR_ARG, "stats is NULL");
+  if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
+  if (!(tol > 0.0)) return fail(DW_ERR_ARG, "tol must be > 0");
+  if (maxit < 1) return fail(DW_ERR_ARG, "maxit must be >= 1");
+  if (mode != DW_F64 && mode != DW_F32 && mode != DW_F16)
+    return fail(DW_ERR_ARG, "unknown mode %d", mode);
+  if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+
+  if (!lat->cg) lat->cg = new (std::nothrow) CGWork();
+  CGWork *w = lat->cg;
+  if (!w) return fail(DW_ERR_ALLOC, "host allocation failed");
+  if (!w->stream && cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "stream create");
+  // order after the caller's stream, then work on the lattice's own stream
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "caller stream synchronize");
+
+  Solve S{lat, w, nrhs, mode, mode == DW_F64 ? DW_F64 : DW_F32, mode == DW_F64 ? 0.0 : 0.1,
+          tol, maxit, mf, w->stream, BlasCtx(lat->V5, nrhs, lat->num_sms)};
+  const size_t f64 = field_bytes(lat, DW_F64, nrhs);
+  const size_t fpp = field_bytes(lat, S.pp, nrhs);
+  const size_t fpr = field_bytes(lat, S.pr, nrhs);
+  int rc;
+  if ((rc = ensure(&w->r64, &w->r64_cap, f64)) || (rc = ensure(&w->Ax64, &w->Ax64_cap, f64)) ||
+      (rc = ensure(&w->tmp64, &w->tmp64_cap, f64)) || (rc = ensure(&w->p, &w->p_cap, fpp)) ||
+      (rc = ensure(&w->Ap, &w->Ap_cap, fpp)) || (rc = ensure(&w->tmp, &w->tmp_cap, fpp)) ||
+      (rc = ensure(&w->rs, &w->rs_cap, fpr)) || (rc = ensure(&w->xs, &w->xs_cap, fpr)) ||
+      (rc = ensure((void **)&w->partials, &w->partials_cap,
+                   sizeof(double) * (size_t)S.c.nblk * nrhs)) ||
+      (rc = ensure((void **)&w->sums, &w->sums_cap, sizeof(double) * nrhs)) ||
+      (rc = ensure((void **)&w->state, &w->state_cap, sizeof(CGState) * nrhs)))
+    return rc;
+  cudaStream_t st = w->stream;
+
+  // |b| per RHS
+  std::vector<double> b2(nrhs);
+  if (blas_redot(S.c, DW_F64, b, DW_F64, b, w->partials, nullptr, st) ||
+      blas_finalize_sum(S.c, w->partials, w->sums, st))
+    return cuda_fail(cudaGetLastError(), "norm launch");
+  e = cudaMemcpyAsync(b2.data(), w->sums, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "norm readback");
+
+  std::vector<CGState> hs(nrhs);
+  const size_t rhs64 = field_bytes(lat, DW_F64, 1);
+  for (int r = 0; r < nrhs; ++r) {
+    CGState &s = hs[r];
+    memset(&s, 0, sizeof(s));
+    s.sigma = 1.0;
+    s.bnorm = std::sqrt(b2[r]);
+    if (!std::isfinite(b2[r])) {
+      s.breakdown = 1;
+    } else if (b2[r] == 0.0) {
+      s.converged = 1;  // b = 0: x = 0 is the solution
+      cudaMemsetAsync((char *)x + (size_t)r * rhs64, 0, rhs64, st);
+    } else {
+      s.active = 1;
+      s.need_update = 1;
+    }
+  }
+  if (cudaMemcpyAsync(w->state, hs.data(), sizeof(CGState) * nrhs, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(w->p, 0, fpp, st) != cudaSuccess ||
+      cudaMemsetAsync(w->xs, 0, fpr, st) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "solver setup");
+
+  // initial residual
+  if ((rc = S.reliable(x, b, 1))) return rc;
+
+  // capture one inner iteration as a graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "begin capture");
+  rc = S.iteration();
+  cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+
+  // host loop: replay, check flags, run reliable updates
+  const long long max_rounds = 4LL * maxit + 64;
+  long long rounds = 0;
+  rc = DW_OK;
+  while (true) {
+    e = cudaMemcpyAsync(hs.data(), w->state, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "state readback");
+      break;
+    }
+    bool any_active = false, any_update = false;
+    for (const CGState &s : hs) {
+      any_active |= s.active != 0;
+      any_update |= (s.active && s.need_update);
+    }
+    if (!any_active) break;
+    if (++rounds > max_rounds) {
+      rc = fail(DW_ERR_STATE, "solver made no progress");
+      break;
+    }
+    if (any_update) {
+      if ((rc = S.reliable(x, b, 0))) break;
+      continue;
+    }
+    for (int k = 0; k < kReplay; ++k) {
+      e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "graph launch");
+      break;
+    }
+  }
+  cudaGraphExecDestroy(exec);
+  if (rc) return rc;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "solver synchronize");
+
+  const double secs =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  bool any_break = false, all_conv = true;
+  for (int r = 0; r < nrhs; ++r) {
+    const CGState &s = hs[r];
+    stats[r].iters = s.iters;
+    stats[r].reliable_updates = s.reliable;
+    stats[r].converged = s.converged;
+    stats[r].true_resid = s.bnorm > 0.0 ? std::sqrt(s.true_r2) / s.bnorm : 0.0;
+    stats[r].seconds = secs;
+    any_break |= s.breakdown != 0;
+    all_conv &= s.converged != 0;
+  }
+  if (any_break) return fail(DW_ERR_BREAKDOWN, "CG breakdown (non-finite or non-positive <p, Ap>)");
+  if (!all_conv) return fail(DW_ERR_NOT_CONVERGED, "CG reached maxit before tol");
+  return DW_OK;
 }

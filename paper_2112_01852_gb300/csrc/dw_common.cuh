@@ -169,17 +169,18 @@ constexpr int kMaxRhsPerLaunch = 64;
 
 // Launch configuration chosen by the tuner.
 struct TileConfig {
-  int spt;  // fifth-dimension slices per thread
-  int tx;   // 4D sites per CTA (multiple of 32)
+  int spt;      // fifth-dimension slices per thread
+  int tx;       // 4D sites per CTA (multiple of 32)
+  int variant;  // hop-phase load scheme, 0 .. kNumVariants-1 (see dw.h)
 };
+constexpr int kNumVariants = 4;
 
-int launch_dslash_f64(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
-int launch_dslash_f32(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
-int launch_dslash_f16(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
-// Largest CTA the stencil kernel (op, spt) can launch with (0 if unknown).
-int dslash_max_threads_f64(int op, int spt);
-int dslash_max_threads_f32(int op, int spt);
-int dslash_max_threads_f16(int op, int spt);
+// Stencil launch at precision `prec`: 0 on success, -2 for a tile/variant
+// that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA
+// launch error.
+int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
+// Largest CTA the stencil kernel (op, spt, variant) can launch (0: none).
+int dslash_max_threads(int prec, int op, int spt, int variant);
 
 struct CGWork;
 

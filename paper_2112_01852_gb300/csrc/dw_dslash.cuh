@@ -3,9 +3,10 @@
 // reconstruction, Table 3), fused with the 5D hop and diagonal terms of the
 // Shamir / Moebius operator.
 //
-// Work decomposition.  A CTA owns `tx` consecutive 4D sites and all Ls slices;
-// thread (x, y) handles 4D site x4 = blockIdx.x*tx + x and the `SPT`
-// consecutive slices s0 = y*SPT .. s0+SPT-1 of right-hand side blockIdx.y.
+// Work decomposition.  A CTA owns `tx` consecutive 4D sites and all Ls slices
+// of one right-hand side (CTAs are numbered RHS-fastest); thread (x, y)
+// handles one 4D site and the `SPT` consecutive slices s0 = y*SPT ..
+// s0+SPT-1.
 // Each link is loaded once per thread and reused across its SPT slices; the
 // Ls/SPT threads of one site read the same link words, so it leaves HBM once.
 // Fermion planes are [p][s][x4], so a warp (32 consecutive x4 at one s)
@@ -18,133 +19,228 @@
 // Dhop uses S = -1 forward and S = +1 backward; Dhop^+ the opposite.
 #pragma once
 
+#include <type_traits>
+
 #include "dw_common.cuh"
 
 namespace dw {
 
-// h index: (spin j * 3 + colour) * 2 + re/im, j in {0, 1}.
-#define RE(a, j, c) a[((j)*3 + (c)) * 2]
-#define IM(a, j, c) a[((j)*3 + (c)) * 2 + 1]
+// ---------------------------------------------------------------------------
+// Register form of a spinor.  A half spinor (2 spins x 3 colours) is held as
+// spin pairs: re[c] = (Re psi_{j=0,c}, Re psi_{j=1,c}), im[c] likewise.  For
+// FP32 arithmetic a pair is a float2 and the arithmetic below compiles to the
+// packed f32x2 instructions (two lanes per instruction); for FP64 it is a
+// double2 worked lane by lane.  This is also the memory order of a quad
+// (4 reals) of the internal layout, so loads land in registers unshuffled.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 p_add(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 p_mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x, a.y * b.y);
+}
+__device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <class V2, class C>
+__device__ __forceinline__ V2 bc(C v) {
+  V2 r;
+  r.x = v;
+  r.y = v;
+  return r;
+}
+template <class V2, class C>
+__device__ __forceinline__ V2 pr(C x, C y) {
+  V2 r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
 
-template <int MU, int S, class C>
-__device__ __forceinline__ void project(C *h, const C *u, const C *l) {
+template <class V2>
+struct Half {
+  V2 re[3];
+  V2 im[3];
+};
+template <class V2>
+struct Spinor {
+  Half<V2> up;  // spins 0, 1 (P+)
+  Half<V2> lo;  // spins 2, 3 (P-)
+};
+
+template <class P>
+struct Pair {
+  using type = typename std::conditional<std::is_same<typename P::C, double>::value, double2,
+                                         float2>::type;
+};
+
+// h = u + S e_mu l   (the half spinor of (1 + S g_mu) psi)
+template <int MU, int S, class V2>
+__device__ __forceinline__ void project(Half<V2> &h, const Half<V2> &u, const Half<V2> &l) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     if (MU == 0) {  // e l = (i l1, i l0)
-      RE(h, 0, c) = RE(u, 0, c) - S * IM(l, 1, c);
-      IM(h, 0, c) = IM(u, 0, c) + S * RE(l, 1, c);
-      RE(h, 1, c) = RE(u, 1, c) - S * IM(l, 0, c);
-      IM(h, 1, c) = IM(u, 1, c) + S * RE(l, 0, c);
+      h.re[c].x = u.re[c].x - S * l.im[c].y;
+      h.im[c].x = u.im[c].x + S * l.re[c].y;
+      h.re[c].y = u.re[c].y - S * l.im[c].x;
+      h.im[c].y = u.im[c].y + S * l.re[c].x;
     } else if (MU == 1) {  // e l = (l1, -l0)
-      RE(h, 0, c) = RE(u, 0, c) + S * RE(l, 1, c);
-      IM(h, 0, c) = IM(u, 0, c) + S * IM(l, 1, c);
-      RE(h, 1, c) = RE(u, 1, c) - S * RE(l, 0, c);
-      IM(h, 1, c) = IM(u, 1, c) - S * IM(l, 0, c);
-    } else if (MU == 2) {  // e l = (i l0, -i l1)
-      RE(h, 0, c) = RE(u, 0, c) - S * IM(l, 0, c);
-      IM(h, 0, c) = IM(u, 0, c) + S * RE(l, 0, c);
-      RE(h, 1, c) = RE(u, 1, c) + S * IM(l, 1, c);
-      IM(h, 1, c) = IM(u, 1, c) - S * RE(l, 1, c);
-    } else {  // e l = (l0, l1)
-      RE(h, 0, c) = RE(u, 0, c) + S * RE(l, 0, c);
-      IM(h, 0, c) = IM(u, 0, c) + S * IM(l, 0, c);
-      RE(h, 1, c) = RE(u, 1, c) + S * RE(l, 1, c);
-      IM(h, 1, c) = IM(u, 1, c) + S * IM(l, 1, c);
+      h.re[c].x = u.re[c].x + S * l.re[c].y;
+      h.im[c].x = u.im[c].x + S * l.im[c].y;
+      h.re[c].y = u.re[c].y - S * l.re[c].x;
+      h.im[c].y = u.im[c].y - S * l.im[c].x;
+    } else if (MU == 2) {  // e l = (i l0, -i l1): lanes stay in place
+      h.re[c] = p_fma(pr<V2>(-S, S), l.im[c], u.re[c]);
+      h.im[c] = p_fma(pr<V2>(S, -S), l.re[c], u.im[c]);
+    } else {  // e l = l
+      h.re[c] = p_fma(bc<V2>(S), l.re[c], u.re[c]);
+      h.im[c] = p_fma(bc<V2>(S), l.im[c], u.im[c]);
     }
   }
 }
 
-// acc (24 reals: upper spins 0..11, lower spins 12..23) += (w, S e_mu^+ w).
-template <int MU, int S, bool FIRST, class C>
-__device__ __forceinline__ void reconstruct(C *acc, const C *w) {
-  C *up = acc;
-  C *lo = acc + 12;
-#pragma unroll
-  for (int i = 0; i < 12; ++i) up[i] = FIRST ? w[i] : up[i] + w[i];
+// acc += (w, S e_mu^+ w)   (FIRST: acc = ...)
+template <int MU, int S, bool FIRST, class V2>
+__device__ __forceinline__ void reconstruct(Spinor<V2> &acc, const Half<V2> &w) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    C r0, i0, r1, i1;  // lower spin 0 and 1 increments
-    if (MU == 0) {  // e^+ w = (-i w1, -i w0)
-      r0 = S * IM(w, 1, c);
-      i0 = -S * RE(w, 1, c);
-      r1 = S * IM(w, 0, c);
-      i1 = -S * RE(w, 0, c);
-    } else if (MU == 1) {  // e^+ w = (-w1, w0)
-      r0 = -S * RE(w, 1, c);
-      i0 = -S * IM(w, 1, c);
-      r1 = S * RE(w, 0, c);
-      i1 = S * IM(w, 0, c);
-    } else if (MU == 2) {  // e^+ w = (-i w0, i w1)
-      r0 = S * IM(w, 0, c);
-      i0 = -S * RE(w, 0, c);
-      r1 = -S * IM(w, 1, c);
-      i1 = S * RE(w, 1, c);
-    } else {  // e^+ w = (w0, w1)
-      r0 = S * RE(w, 0, c);
-      i0 = S * IM(w, 0, c);
-      r1 = S * RE(w, 1, c);
-      i1 = S * IM(w, 1, c);
-    }
     if (FIRST) {
-      RE(lo, 0, c) = r0;
-      IM(lo, 0, c) = i0;
-      RE(lo, 1, c) = r1;
-      IM(lo, 1, c) = i1;
+      acc.up.re[c] = w.re[c];
+      acc.up.im[c] = w.im[c];
     } else {
-      RE(lo, 0, c) += r0;
-      IM(lo, 0, c) += i0;
-      RE(lo, 1, c) += r1;
-      IM(lo, 1, c) += i1;
+      acc.up.re[c] = p_add(acc.up.re[c], w.re[c]);
+      acc.up.im[c] = p_add(acc.up.im[c], w.im[c]);
     }
-  }
-}
-
-// w = U h (ADJ = false) or U^+ h (ADJ = true) for both spins; U is 18 reals,
-// index (row * 3 + col) * 2 + re/im.
-template <bool ADJ, class C>
-__device__ __forceinline__ void su3_mul(C *w, const C *U, const C *h) {
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      C re = 0, im = 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int idx = ADJ ? (k * 3 + r) : (r * 3 + k);
-        const C ur = U[idx * 2], ui = U[idx * 2 + 1];
-        const C hr = RE(h, j, k), hi = IM(h, j, k);
-        if (!ADJ) {
-          re += ur * hr - ui * hi;
-          im += ur * hi + ui * hr;
-        } else {
-          re += ur * hr + ui * hi;
-          im += ur * hi - ui * hr;
-        }
+    V2 dre, dim;  // lower-spin increment S e^+ w
+    bool packed = false;
+    if (MU == 0) {  // e^+ w = (-i w1, -i w0)
+      dre = pr<V2>(S * w.im[c].y, S * w.im[c].x);
+      dim = pr<V2>(-S * w.re[c].y, -S * w.re[c].x);
+    } else if (MU == 1) {  // e^+ w = (-w1, w0)
+      dre = pr<V2>(-S * w.re[c].y, S * w.re[c].x);
+      dim = pr<V2>(-S * w.im[c].y, S * w.im[c].x);
+    } else {
+      packed = true;
+    }
+    if (!packed) {
+      if (FIRST) {
+        acc.lo.re[c] = dre;
+        acc.lo.im[c] = dim;
+      } else {
+        acc.lo.re[c].x += dre.x;
+        acc.lo.re[c].y += dre.y;
+        acc.lo.im[c].x += dim.x;
+        acc.lo.im[c].y += dim.y;
       }
-      RE(w, j, r) = re;
-      IM(w, j, r) = im;
+    } else if (MU == 2) {  // e^+ w = (-i w0, i w1)
+      if (FIRST) {
+        acc.lo.re[c] = p_mul(pr<V2>(S, -S), w.im[c]);
+        acc.lo.im[c] = p_mul(pr<V2>(-S, S), w.re[c]);
+      } else {
+        acc.lo.re[c] = p_fma(pr<V2>(S, -S), w.im[c], acc.lo.re[c]);
+        acc.lo.im[c] = p_fma(pr<V2>(-S, S), w.re[c], acc.lo.im[c]);
+      }
+    } else {  // e^+ w = w
+      if (FIRST) {
+        acc.lo.re[c] = p_mul(bc<V2>(S), w.re[c]);
+        acc.lo.im[c] = p_mul(bc<V2>(S), w.im[c]);
+      } else {
+        acc.lo.re[c] = p_fma(bc<V2>(S), w.re[c], acc.lo.re[c]);
+        acc.lo.im[c] = p_fma(bc<V2>(S), w.im[c], acc.lo.im[c]);
+      }
     }
   }
 }
 
-#undef RE
-#undef IM
+// w = U h (ADJ = false) or U^+ h (ADJ = true), both spins at once.  U holds
+// 18 reals, element (row, col) at (row * 3 + col) * 2 + re/im.
+template <bool ADJ, class V2, class C>
+__device__ __forceinline__ void su3_mul(Half<V2> &w, const C *U, const Half<V2> &h) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    V2 wr, wi;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int idx = ADJ ? (k * 3 + r) : (r * 3 + k);
+      const C ur = U[idx * 2];
+      const C ui = ADJ ? -U[idx * 2 + 1] : U[idx * 2 + 1];
+      // (ur + i ui)(hre + i him): re = ur hre - ui him, im = ur him + ui hre
+      if (k == 0) {
+        wr = p_mul(bc<V2>(ur), h.re[k]);
+        wi = p_mul(bc<V2>(ur), h.im[k]);
+      } else {
+        wr = p_fma(bc<V2>(ur), h.re[k], wr);
+        wi = p_fma(bc<V2>(ur), h.im[k], wi);
+      }
+      wr = p_fma(bc<V2>(-ui), h.im[k], wr);
+      wi = p_fma(bc<V2>(ui), h.re[k], wi);
+    }
+    w.re[r] = wr;
+    w.im[r] = wi;
+  }
+}
+
+// Memory <-> registers.  A quad (4 reals, one colour of one chirality half) is
+// one vec for F32 / F16 and two vecs (planes 2q, 2q+1) for F64.
+__device__ __forceinline__ void quad_in(float2 &re, float2 &im, const float4 *p, long long) {
+  const float4 v = __ldg(p);
+  re = make_float2(v.x, v.y);
+  im = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void quad_in(float2 &re, float2 &im, const uint2 *p, long long) {
+  const uint2 v = __ldg(p);
+  re = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+  im = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+}
+__device__ __forceinline__ void quad_in(double2 &re, double2 &im, const double2 *p,
+                                        long long plane) {
+  re = __ldg(p);
+  im = __ldg(p + plane);
+}
+__device__ __forceinline__ void quad_out(float4 *p, long long, float2 re, float2 im) {
+  *p = make_float4(re.x, re.y, im.x, im.y);
+}
+__device__ __forceinline__ void quad_out(uint2 *p, long long, float2 re, float2 im) {
+  __half2 a = __float22half2_rn(re);
+  __half2 b = __float22half2_rn(im);
+  uint2 v;
+  v.x = *reinterpret_cast<unsigned int *>(&a);
+  v.y = *reinterpret_cast<unsigned int *>(&b);
+  *p = v;
+}
+__device__ __forceinline__ void quad_out(double2 *p, long long plane, double2 re, double2 im) {
+  p[0] = re;
+  p[plane] = im;
+}
 
 template <class P>
 struct Field {
   using vec = typename P::vec;
-  using C = typename P::C;
-  static constexpr int NHP = 12 / P::R;  // vecs per half spinor
+  using V2 = typename Pair<P>::type;
+  static constexpr int VPQ = 4 / P::R;  // vecs (planes) per quad
   const vec *base;
   long long plane;
   int V4;
-  // 12 reals of the upper (half = 0) or lower (half = 1) spins at (x4, s).
-  __device__ __forceinline__ void load_half(C *h, int x4, int s, int half) const {
-    const vec *p = base + (long long)half * NHP * plane + (long long)s * V4 + x4;
+  // half = 0: upper spins, 1: lower spins, at (x4, s)
+  __device__ __forceinline__ void load_half(Half<V2> &h, int x4, int s, int half) const {
+    const vec *p = base + (long long)half * 3 * VPQ * plane + (long long)s * V4 + x4;
 #pragma unroll
-    for (int q = 0; q < NHP; ++q) load_vec<P>(h + q * P::R, p + q * plane);
+    for (int c = 0; c < 3; ++c) quad_in(h.re[c], h.im[c], p + (long long)c * VPQ * plane, plane);
   }
 };
+
+template <class P>
+__device__ __forceinline__ void store_spinor(typename P::vec *base, long long plane,
+                                             const Spinor<typename Pair<P>::type> &v) {
+  constexpr int VPQ = 4 / P::R;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    quad_out(base + (long long)c * VPQ * plane, plane, v.up.re[c], v.up.im[c]);
+    quad_out(base + (long long)(3 + c) * VPQ * plane, plane, v.lo.re[c], v.lo.im[c]);
+  }
+}
 
 template <class P>
 __device__ __forceinline__ void load_link(typename P::C *U, const typename P::vec *gmain,
@@ -157,39 +253,48 @@ __device__ __forceinline__ void load_link(typename P::C *U, const typename P::ve
   widen_t(__ldg(gtail + (long long)mu * V4 + x4), U + 16);
 }
 
+template <class V2>
+__device__ __forceinline__ void half_axpby(Half<V2> &o, V2 a, const Half<V2> &x, V2 b,
+                                          const Half<V2> &y) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o.re[c] = p_fma(a, x.re[c], p_mul(b, y.re[c]));
+    o.im[c] = p_fma(a, x.im[c], p_mul(b, y.im[c]));
+  }
+}
+
 // Rolling evaluation of A psi_s + B [K psi]_s (KDAG = false) or
 // A psi_s + B [K^+ psi]_s (KDAG = true) at 4D site x4 for s = s0 .. s0+SPT-1.
 //   K:   upper from s-1, lower from s+1;  K^+: upper from s+1, lower from s-1;
 //   a neighbour index that leaves [0, Ls) wraps and carries -mf.
-// Calls f(j, v) with the 24 reals of slice s0 + j.  Each half spinor is loaded
+// Calls f(j, v) with the spinor of slice s0 + j.  Each half spinor is loaded
 // once: 2 (SPT + 1) half-spinor loads for SPT slices.
 template <class P, bool KDAG, int SPT, class Fn>
 __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int Ls,
                                         typename P::C A, typename P::C B,
                                         typename P::C mf, Fn &&f) {
   using C = typename P::C;
-  // "carry" half: the one whose partner slice is below s (s - 1)
-  //   K:   upper(s-1) is carried; lower(s+1) is loaded ahead.
-  //   K^+: lower(s-1) is carried; upper(s+1) is loaded ahead.
+  using V2 = typename Pair<P>::type;
+  // K: the upper half comes from s-1 (carried), the lower from s+1 (loaded ahead);
+  // K^+: the other way round.
   const int carry_half = KDAG ? 1 : 0;
   const int ahead_half = KDAG ? 0 : 1;
-  C prev[12], cur_ahead[12];
+  Half<V2> prev, cur_ahead;
+  C fp = 1;
   {
     int sp = s0 - 1;
-    C f0 = 1;
     if (sp < 0) {
       sp = Ls - 1;
-      f0 = -mf;
+      fp = -mf;
     }
     F.load_half(prev, x4, sp, carry_half);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) prev[i] *= f0;
-    F.load_half(cur_ahead, x4, s0, ahead_half);  // the ahead half at s itself
+    F.load_half(cur_ahead, x4, s0, ahead_half);
   }
+  const V2 vA = bc<V2>(A);
 #pragma unroll
   for (int j = 0; j < SPT; ++j) {
     const int s = s0 + j;
-    C cur_carry[12], next_ahead[12];
+    Half<V2> cur_carry, next_ahead;
     F.load_half(cur_carry, x4, s, carry_half);
     int sn = s + 1;
     C fn = 1;
@@ -198,20 +303,14 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
       fn = -mf;
     }
     F.load_half(next_ahead, x4, sn, ahead_half);
-    C v[24];
-    C *vc = v + 12 * carry_half;
-    C *va = v + 12 * ahead_half;
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      vc[i] = A * cur_carry[i] + B * prev[i];
-      va[i] = A * cur_ahead[i] + (B * fn) * next_ahead[i];
-    }
+    Spinor<V2> v;
+    Half<V2> &vc = KDAG ? v.lo : v.up;
+    Half<V2> &va = KDAG ? v.up : v.lo;
+    half_axpby(vc, vA, cur_carry, bc<V2>(B * (j == 0 ? fp : C(1))), prev);
+    half_axpby(va, vA, cur_ahead, bc<V2>(B * fn), next_ahead);
     f(j, v);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      prev[i] = cur_carry[i];
-      cur_ahead[i] = next_ahead[i];
-    }
+    prev = cur_carry;
+    cur_ahead = next_ahead;
   }
 }
 
@@ -219,17 +318,18 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
 // where W = U_mu(l4) (ADJ = false) or U_mu(l4)^+ (ADJ = true) and psi' is psi
 // itself (PHI = false) or phi = (b + cK) psi (PHI = true).
 template <class P, int MU, int S, bool ADJ, bool PHI, bool FIRST, int SPT>
-__device__ __forceinline__ void hop_dir(typename P::C (&acc)[SPT][24], const Field<P> &F,
-                                        const typename P::vec *gmain,
+__device__ __forceinline__ void hop_dir(Spinor<typename Pair<P>::type> (&acc)[SPT],
+                                        const Field<P> &F, const typename P::vec *gmain,
                                         const typename P::tvec *gtail, int y4, int l4, int s0,
                                         int Ls, typename P::C b, typename P::C c,
                                         typename P::C mf) {
   using C = typename P::C;
+  using V2 = typename Pair<P>::type;
   C U[18];
   load_link<P>(U, gmain, gtail, MU, l4, F.V4);
-  auto body = [&](int j, const C *v) {
-    C h[12], w[12];
-    project<MU, S>(h, v, v + 12);
+  auto body = [&](int j, const Spinor<V2> &v) {
+    Half<V2> h, w;
+    project<MU, S>(h, v.up, v.lo);
     su3_mul<ADJ>(w, U, h);
     reconstruct<MU, S, FIRST>(acc[j], w);
   };
@@ -238,30 +338,291 @@ __device__ __forceinline__ void hop_dir(typename P::C (&acc)[SPT][24], const Fie
   } else {
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
-      C v[24];
-      F.load_half(v, y4, s0 + j, 0);
-      F.load_half(v + 12, y4, s0 + j, 1);
+      Spinor<V2> v;
+      F.load_half(v.up, y4, s0 + j, 0);
+      F.load_half(v.lo, y4, s0 + j, 1);
       body(j, v);
     }
   }
 }
 
+// ---------------------------------------------------------------------------
+// Staged variant of the hop phase.  Each thread copies the link and the
+// neighbour spinors of the next direction into its own shared-memory slots
+// with cp.async (16-byte LDGSTS; 8/4-byte for the link tail and FP16 quads)
+// while it computes the current direction from the previous slot set, so the
+// loads of a whole direction are in flight without holding registers.  Slots
+// are [stage][slot][thread], so a warp's accesses to one slot are contiguous
+// and free of bank conflicts.  Every thread reads only what it copied itself:
+// cp.async.wait_group is the only synchronisation needed.
+constexpr int kStages = 2;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <class P, bool PHI, int SPT>
+struct StageLayout {
+  static constexpr int VPQ = 4 / P::R;
+  static constexpr int NM = 16 / P::R;  // link vec planes
+  // spinor vec slots per direction: full spinors (Dhop) or the halves that the
+  // rolling (b + cK) combination needs: upper s0-1 .. s0+SPT-1, lower s0 .. s0+SPT
+  static constexpr int NSP = PHI ? 6 * (SPT + 1) * VPQ : 6 * SPT * VPQ;
+  static constexpr int NVEC = NSP + NM;
+  static __host__ __device__ size_t stage_bytes(int T) {
+    size_t b = (size_t)NVEC * T * sizeof(typename P::vec) + (size_t)T * sizeof(typename P::tvec);
+    return (b + 15) & ~(size_t)15;
+  }
+};
+
 template <class P, int OP, int SPT>
+struct StagedHop {
+  using C = typename P::C;
+  using vec = typename P::vec;
+  using tvec = typename P::tvec;
+  using V2 = typename Pair<P>::type;
+  static constexpr bool PHI = (OP == OP_D);
+  using L = StageLayout<P, PHI, SPT>;
+  static constexpr int VPQ = L::VPQ;
+  unsigned char *smem;  // kStages stages
+  int T, t;             // threads per CTA, this thread's slot column
+  __device__ __forceinline__ vec *vslot(int stage, int k) const {
+    return reinterpret_cast<vec *>(smem + (size_t)stage * L::stage_bytes(T)) + (size_t)k * T + t;
+  }
+  __device__ __forceinline__ tvec *tslot(int stage) const {
+    return reinterpret_cast<tvec *>(smem + (size_t)stage * L::stage_bytes(T) +
+                                    (size_t)L::NVEC * T * sizeof(vec)) + t;
+  }
+  __device__ __forceinline__ void issue(int stage, const Field<P> &F, const vec *gmain,
+                                        const tvec *gtail, int mu, int y4, int l4, int s0,
+                                        int Ls) const {
+    const vec *lp = gmain + (long long)mu * L::NM * F.V4 + l4;
+#pragma unroll
+    for (int q = 0; q < L::NM; ++q) cp_async<sizeof(vec)>(vslot(stage, L::NSP + q), lp + (long long)q * F.V4);
+    cp_async<sizeof(tvec)>(tslot(stage), gtail + (long long)mu * F.V4 + l4);
+    if (!PHI) {
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        const vec *sp = F.base + (long long)(s0 + j) * F.V4 + y4;
+#pragma unroll
+        for (int k = 0; k < 6 * VPQ; ++k)
+          cp_async<sizeof(vec)>(vslot(stage, j * 6 * VPQ + k), sp + (long long)k * F.plane);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i <= SPT; ++i) {
+        int su = s0 - 1 + i;
+        if (su < 0) su = Ls - 1;
+        int sl = s0 + i;
+        if (sl == Ls) sl = 0;
+        const vec *pu = F.base + (long long)su * F.V4 + y4;
+        const vec *pl = F.base + (long long)sl * F.V4 + y4 + (long long)3 * VPQ * F.plane;
+#pragma unroll
+        for (int k = 0; k < 3 * VPQ; ++k) {
+          cp_async<sizeof(vec)>(vslot(stage, i * 3 * VPQ + k), pu + (long long)k * F.plane);
+          cp_async<sizeof(vec)>(vslot(stage, (SPT + 1 + i) * 3 * VPQ + k),
+                                pl + (long long)k * F.plane);
+        }
+      }
+    }
+  }
+  __device__ __forceinline__ void read_half(Half<V2> &h, int stage, int k0) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) read_quad(h.re[c], h.im[c], stage, k0 + c * VPQ);
+  }
+  __device__ __forceinline__ void read_quad(float2 &re, float2 &im, int stage, int k) const {
+    if (sizeof(vec) == 16) {
+      const float4 v = *reinterpret_cast<const float4 *>(vslot(stage, k));
+      re = make_float2(v.x, v.y);
+      im = make_float2(v.z, v.w);
+    } else {
+      const uint2 v = *reinterpret_cast<const uint2 *>(vslot(stage, k));
+      re = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+      im = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    }
+  }
+  __device__ __forceinline__ void read_quad(double2 &re, double2 &im, int stage, int k) const {
+    re = *reinterpret_cast<const double2 *>(vslot(stage, k));
+    im = *reinterpret_cast<const double2 *>(vslot(stage, k + 1));
+  }
+  __device__ __forceinline__ void read_link(C *U, int stage) const {
+#pragma unroll
+    for (int q = 0; q < L::NM; ++q) widen(*vslot(stage, L::NSP + q), U + q * P::R);
+    widen_t(*tslot(stage), U + 16);
+  }
+};
+
+// Hop phase with the staged loads: the 8 directions in the order t, z, y, x
+// (forward then backward), kStages-deep cp.async pipeline.
+template <class P, int OP, int SPT>
+__device__ __forceinline__ void hop_staged(Spinor<typename Pair<P>::type> (&acc)[SPT],
+                                           const StagedHop<P, OP, SPT> &H, const Field<P> &F,
+                                           const typename P::vec *gmain,
+                                           const typename P::tvec *gtail, int x4, bool active,
+                                           const int (&nb)[8], int s0, int Ls,
+                                           typename P::C b, typename P::C c, typename P::C mf) {
+  using C = typename P::C;
+  using V2 = typename Pair<P>::type;
+  constexpr bool DAG = (OP == OP_DHOP_DAG || OP == OP_DDAG);
+  constexpr bool PHI = (OP == OP_D);
+  constexpr int SF = DAG ? 1 : -1;
+  constexpr int SB = -SF;
+  // direction d: mu = 3 - d/2; even d forward (link at x4), odd d backward
+#pragma unroll
+  for (int d = 0; d < kStages - 1; ++d) {
+    if (active) H.issue(d % kStages, F, gmain, gtail, 3 - d / 2, nb[d], (d & 1) ? nb[d] : x4, s0, Ls);
+    cp_async_commit();
+  }
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const int dn = d + kStages - 1;
+    if (dn < 8 && active)
+      H.issue(dn % kStages, F, gmain, gtail, 3 - dn / 2, nb[dn < 8 ? dn : 0],
+              (dn & 1) ? nb[dn < 8 ? dn : 0] : x4, s0, Ls);
+    cp_async_commit();
+    cp_async_wait<kStages - 1>();
+    if (!active) continue;
+    const int stg = d % kStages;
+    C U[18];
+    H.read_link(U, stg);
+    auto body = [&](int j, const Spinor<V2> &v) {
+      Half<V2> h, w;
+      switch (d) {
+        case 0: project<3, SF>(h, v.up, v.lo); su3_mul<false>(w, U, h); reconstruct<3, SF, true>(acc[j], w); break;
+        case 1: project<3, SB>(h, v.up, v.lo); su3_mul<true>(w, U, h); reconstruct<3, SB, false>(acc[j], w); break;
+        case 2: project<2, SF>(h, v.up, v.lo); su3_mul<false>(w, U, h); reconstruct<2, SF, false>(acc[j], w); break;
+        case 3: project<2, SB>(h, v.up, v.lo); su3_mul<true>(w, U, h); reconstruct<2, SB, false>(acc[j], w); break;
+        case 4: project<1, SF>(h, v.up, v.lo); su3_mul<false>(w, U, h); reconstruct<1, SF, false>(acc[j], w); break;
+        case 5: project<1, SB>(h, v.up, v.lo); su3_mul<true>(w, U, h); reconstruct<1, SB, false>(acc[j], w); break;
+        case 6: project<0, SF>(h, v.up, v.lo); su3_mul<false>(w, U, h); reconstruct<0, SF, false>(acc[j], w); break;
+        default: project<0, SB>(h, v.up, v.lo); su3_mul<true>(w, U, h); reconstruct<0, SB, false>(acc[j], w); break;
+      }
+    };
+    if (!PHI) {
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        Spinor<V2> v;
+        H.read_half(v.up, stg, j * 6 * H.VPQ);
+        H.read_half(v.lo, stg, j * 6 * H.VPQ + 3 * H.VPQ);
+        body(j, v);
+      }
+    } else {
+      const V2 vb = bc<V2>(b);
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        Half<V2> up_prev, up_cur, lo_cur, lo_next;
+        H.read_half(up_prev, stg, j * 3 * H.VPQ);
+        H.read_half(up_cur, stg, (j + 1) * 3 * H.VPQ);
+        H.read_half(lo_cur, stg, (SPT + 1 + j) * 3 * H.VPQ);
+        H.read_half(lo_next, stg, (SPT + 2 + j) * 3 * H.VPQ);
+        const C fp = (j == 0 && s0 == 0) ? -mf : C(1);
+        const C fn = (s0 + j + 1 == Ls) ? -mf : C(1);
+        Spinor<V2> v;
+        half_axpby(v.up, vb, up_cur, bc<V2>(c * fp), up_prev);
+        half_axpby(v.lo, vb, lo_cur, bc<V2>(c * fn), lo_next);
+        body(j, v);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Register-prefetch variant of the hop phase (Dhop, Dhop^+ and the hop of D^+,
+// which act on psi itself): the 8 x SPT (direction, slice) steps are walked in
+// order and the spinor (and, at a new direction, the link) of step k+1 is
+// loaded before step k is computed, so one step's loads are always in flight
+// behind the arithmetic.  ORDER 0 visits t, z, y, x; ORDER 1 visits x, y, z, t.
+template <class P, int SPT, int ORDER, bool DAG>
+__device__ __forceinline__ void hop_prefetch(Spinor<typename Pair<P>::type> (&acc)[SPT],
+                                             const Field<P> &F, const typename P::vec *gmain,
+                                             const typename P::tvec *gtail, int x4,
+                                             const int (&nb)[8], int s0) {
+  using C = typename P::C;
+  using V2 = typename Pair<P>::type;
+  constexpr int SF = DAG ? 1 : -1;
+  constexpr int SB = -SF;
+  constexpr int N = 8 * SPT;
+  auto mu_of = [](int d) { return ORDER == 0 ? 3 - d / 2 : d / 2; };
+  auto nb_of = [&](int d) { return nb[(3 - mu_of(d)) * 2 + (d & 1)]; };
+  Spinor<V2> nxt;
+  C Unxt[18];
+  F.load_half(nxt.up, nb_of(0), s0, 0);
+  F.load_half(nxt.lo, nb_of(0), s0, 1);
+  load_link<P>(Unxt, gmain, gtail, mu_of(0), x4, F.V4);
+  C U[18];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int d = k / SPT, j = k % SPT;
+    const Spinor<V2> cur = nxt;
+    if (j == 0) {
+#pragma unroll
+      for (int i = 0; i < 18; ++i) U[i] = Unxt[i];
+    }
+    if (k + 1 < N) {
+      const int d1 = (k + 1) / SPT, j1 = (k + 1) % SPT;
+      F.load_half(nxt.up, nb_of(d1), s0 + j1, 0);
+      F.load_half(nxt.lo, nb_of(d1), s0 + j1, 1);
+      if (j1 == 0) load_link<P>(Unxt, gmain, gtail, mu_of(d1), (d1 & 1) ? nb_of(d1) : x4, F.V4);
+    }
+    Half<V2> h, w;
+    const int mu = mu_of(d);
+    const bool fwd = !(d & 1);
+    // compile-time dispatch (k is a constant after unrolling)
+    if (mu == 3 && fwd) { project<3, SF>(h, cur.up, cur.lo); su3_mul<false>(w, U, h); }
+    if (mu == 3 && !fwd) { project<3, SB>(h, cur.up, cur.lo); su3_mul<true>(w, U, h); }
+    if (mu == 2 && fwd) { project<2, SF>(h, cur.up, cur.lo); su3_mul<false>(w, U, h); }
+    if (mu == 2 && !fwd) { project<2, SB>(h, cur.up, cur.lo); su3_mul<true>(w, U, h); }
+    if (mu == 1 && fwd) { project<1, SF>(h, cur.up, cur.lo); su3_mul<false>(w, U, h); }
+    if (mu == 1 && !fwd) { project<1, SB>(h, cur.up, cur.lo); su3_mul<true>(w, U, h); }
+    if (mu == 0 && fwd) { project<0, SF>(h, cur.up, cur.lo); su3_mul<false>(w, U, h); }
+    if (mu == 0 && !fwd) { project<0, SB>(h, cur.up, cur.lo); su3_mul<true>(w, U, h); }
+    if (d == 0) {
+      if (mu == 3) reconstruct<3, SF, true>(acc[j], w);
+      if (mu == 0) reconstruct<0, SF, true>(acc[j], w);
+    } else {
+      if (mu == 3 && fwd) reconstruct<3, SF, false>(acc[j], w);
+      if (mu == 3 && !fwd) reconstruct<3, SB, false>(acc[j], w);
+      if (mu == 2 && fwd) reconstruct<2, SF, false>(acc[j], w);
+      if (mu == 2 && !fwd) reconstruct<2, SB, false>(acc[j], w);
+      if (mu == 1 && fwd) reconstruct<1, SF, false>(acc[j], w);
+      if (mu == 1 && !fwd) reconstruct<1, SB, false>(acc[j], w);
+      if (mu == 0 && fwd) reconstruct<0, SF, false>(acc[j], w);
+      if (mu == 0 && !fwd) reconstruct<0, SB, false>(acc[j], w);
+    }
+  }
+}
+
+template <class P, int OP, int SPT, int VAR>
 __global__ void dslash_kernel(const DslashParams p) {
   using C = typename P::C;
   using vec = typename P::vec;
   using tvec = typename P::tvec;
+  using V2 = typename Pair<P>::type;
   constexpr bool DAG = (OP == OP_DHOP_DAG || OP == OP_DDAG);
   constexpr bool PHI = (OP == OP_D);
   constexpr int SF = DAG ? 1 : -1;  // sign S of the forward hop
   constexpr int SB = -SF;           // sign S of the backward hop
-  constexpr int NHP = 12 / P::R;
 
+  // CTAs are RHS-major (consecutive CTAs = the same sites for successive RHS),
+  // so the links of a tile are reused from L2 across right-hand sides.
   const int tx = blockDim.x;
-  const int x4 = blockIdx.x * tx + threadIdx.x;
+  const int rhs = blockIdx.x % p.nrhs;
+  const int x4 = (blockIdx.x / p.nrhs) * tx + threadIdx.x;
   const int chunk = threadIdx.y;
   const int nchunk = blockDim.y;
-  const int rhs = blockIdx.y;
   if (p.gate && !p.gate[(long long)rhs * p.gate_stride]) return;  // whole CTA: uniform
   const bool active = x4 < p.V4;
   const int s0 = chunk * SPT;
@@ -280,8 +641,11 @@ __global__ void dslash_kernel(const DslashParams p) {
   const C alpha = (C)(p.b * (4.0 - p.M5) + 1.0);
   const C beta = (C)(p.c * (4.0 - p.M5) - 1.0);
 
-  C acc[SPT][24];
+  Spinor<V2> acc[SPT];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  size_t smem_used = 0;
 
+  int nb[8];  // neighbours in the order t+, t-, z+, z-, y+, y-, x+, x-
   if (active) {
     int rem = x4;
     const int cx = rem % p.L[0];
@@ -293,30 +657,58 @@ __global__ void dslash_kernel(const DslashParams p) {
     const int st1 = p.L[0];
     const int st2 = p.L[0] * p.L[1];
     const int st3 = st2 * p.L[2];
-    const int xf = (cx == p.L[0] - 1) ? x4 - (p.L[0] - 1) : x4 + 1;
-    const int xb = (cx == 0) ? x4 + (p.L[0] - 1) : x4 - 1;
-    const int yf = (cy == p.L[1] - 1) ? x4 - (p.L[1] - 1) * st1 : x4 + st1;
-    const int yb = (cy == 0) ? x4 + (p.L[1] - 1) * st1 : x4 - st1;
-    const int zf = (cz == p.L[2] - 1) ? x4 - (p.L[2] - 1) * st2 : x4 + st2;
-    const int zb = (cz == 0) ? x4 + (p.L[2] - 1) * st2 : x4 - st2;
-    const int tf = (ct == p.L[3] - 1) ? x4 - (p.L[3] - 1) * st3 : x4 + st3;
-    const int tb = (ct == 0) ? x4 + (p.L[3] - 1) * st3 : x4 - st3;
-
-    hop_dir<P, 0, SF, false, PHI, true, SPT>(acc, F, gmain, gtail, xf, x4, s0, Ls, b, c, mf);
-    hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, xb, xb, s0, Ls, b, c, mf);
-    hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, yf, x4, s0, Ls, b, c, mf);
-    hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, yb, yb, s0, Ls, b, c, mf);
-    hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, zf, x4, s0, Ls, b, c, mf);
-    hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, zb, zb, s0, Ls, b, c, mf);
-    hop_dir<P, 3, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, tf, x4, s0, Ls, b, c, mf);
-    hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, tb, tb, s0, Ls, b, c, mf);
+    nb[6] = (cx == p.L[0] - 1) ? x4 - (p.L[0] - 1) : x4 + 1;
+    nb[7] = (cx == 0) ? x4 + (p.L[0] - 1) : x4 - 1;
+    nb[4] = (cy == p.L[1] - 1) ? x4 - (p.L[1] - 1) * st1 : x4 + st1;
+    nb[5] = (cy == 0) ? x4 + (p.L[1] - 1) * st1 : x4 - st1;
+    nb[2] = (cz == p.L[2] - 1) ? x4 - (p.L[2] - 1) * st2 : x4 + st2;
+    nb[3] = (cz == 0) ? x4 + (p.L[2] - 1) * st2 : x4 - st2;
+    nb[0] = (ct == p.L[3] - 1) ? x4 - (p.L[3] - 1) * st3 : x4 + st3;
+    nb[1] = (ct == 0) ? x4 + (p.L[3] - 1) * st3 : x4 - st3;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = 0;
   }
 
-  auto store = [&](int j, const C *v) {
-    vec *o = out + (long long)(s0 + j) * p.V4 + x4;
-#pragma unroll
-    for (int q = 0; q < 2 * NHP; ++q) store_vec<P>(o + q * p.plane, v + q * P::R);
+  if (VAR == 0) {
+    if (active) {
+      hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gmain, gtail, nb[0], x4, s0, Ls, b, c, mf);
+      hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[1], nb[1], s0, Ls, b, c, mf);
+      hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[2], x4, s0, Ls, b, c, mf);
+      hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[3], nb[3], s0, Ls, b, c, mf);
+      hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[4], x4, s0, Ls, b, c, mf);
+      hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[5], nb[5], s0, Ls, b, c, mf);
+      hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[6], x4, s0, Ls, b, c, mf);
+      hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[7], nb[7], s0, Ls, b, c, mf);
+    }
+  } else if (VAR >= 2) {
+    if (PHI) {  // the (b + cK) input combination keeps the VAR 0 path
+      if (active) {
+        hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gmain, gtail, nb[0], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[1], nb[1], s0, Ls, b, c, mf);
+        hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[2], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[3], nb[3], s0, Ls, b, c, mf);
+        hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[4], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[5], nb[5], s0, Ls, b, c, mf);
+        hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[6], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[7], nb[7], s0, Ls, b, c, mf);
+      }
+    } else if (active) {
+      hop_prefetch<P, SPT, VAR == 2 ? 0 : 1, DAG>(acc, F, gmain, gtail, x4, nb, s0);
+    }
+  } else {
+    StagedHop<P, OP, SPT> H;
+    H.smem = smem_raw;
+    H.T = tx * nchunk;
+    H.t = chunk * tx + threadIdx.x;
+    hop_staged<P, OP, SPT>(acc, H, F, gmain, gtail, x4, active, nb, s0, Ls, b, c, mf);
+    smem_used = kStages * StageLayout<P, PHI, SPT>::stage_bytes(H.T);
+  }
+
+  auto store = [&](int j, const Spinor<V2> &v) {
+    store_spinor<P>(out + (long long)(s0 + j) * p.V4 + x4, p.plane, v);
   };
+  const V2 mhalf = bc<V2>(C(-0.5));
 
   if (OP == OP_DHOP || OP == OP_DHOP_DAG) {
     if (active) {
@@ -326,10 +718,15 @@ __global__ void dslash_kernel(const DslashParams p) {
   } else if (OP == OP_D) {
     // out = alpha psi + beta K psi - 1/2 Dhop phi
     if (active) {
-      roll_5d<P, false, SPT>(F, x4, s0, Ls, alpha, beta, mf, [&](int j, const C *v) {
-        C o[24];
+      roll_5d<P, false, SPT>(F, x4, s0, Ls, alpha, beta, mf, [&](int j, const Spinor<V2> &v) {
+        Spinor<V2> o;
 #pragma unroll
-        for (int i = 0; i < 24; ++i) o[i] = v[i] - C(0.5) * acc[j][i];
+        for (int cc = 0; cc < 3; ++cc) {
+          o.up.re[cc] = p_fma(mhalf, acc[j].up.re[cc], v.up.re[cc]);
+          o.up.im[cc] = p_fma(mhalf, acc[j].up.im[cc], v.up.im[cc]);
+          o.lo.re[cc] = p_fma(mhalf, acc[j].lo.re[cc], v.lo.re[cc]);
+          o.lo.im[cc] = p_fma(mhalf, acc[j].lo.im[cc], v.lo.im[cc]);
+        }
         store(j, o);
       });
     }
@@ -337,35 +734,49 @@ __global__ void dslash_kernel(const DslashParams p) {
     // OP_DDAG: out = alpha psi + beta K^+ psi - 1/2 (b + c K^+) Dhop^+ psi.
     // K^+ acc needs the upper spins of slice s+1 and the lower spins of s-1;
     // at chunk edges they come from the neighbouring chunk through shared memory.
-    extern __shared__ unsigned char smem_raw[];
-    C *sm_up = reinterpret_cast<C *>(smem_raw);    // [nchunk][12][tx]
-    C *sm_lo = sm_up + (size_t)nchunk * 12 * tx;   // [nchunk][12][tx]
+    V2 *sm_up = reinterpret_cast<V2 *>(smem_raw + smem_used);  // [nchunk][6][tx]
+    V2 *sm_lo = sm_up + (size_t)nchunk * 6 * tx;    // [nchunk][6][tx]
     const int t = threadIdx.x;
     if (active) {
 #pragma unroll
-      for (int i = 0; i < 12; ++i) {
-        sm_up[((size_t)chunk * 12 + i) * tx + t] = acc[0][i];
-        sm_lo[((size_t)chunk * 12 + i) * tx + t] = acc[SPT - 1][12 + i];
+      for (int cc = 0; cc < 3; ++cc) {
+        sm_up[((size_t)chunk * 6 + 2 * cc) * tx + t] = acc[0].up.re[cc];
+        sm_up[((size_t)chunk * 6 + 2 * cc + 1) * tx + t] = acc[0].up.im[cc];
+        sm_lo[((size_t)chunk * 6 + 2 * cc) * tx + t] = acc[SPT - 1].lo.re[cc];
+        sm_lo[((size_t)chunk * 6 + 2 * cc + 1) * tx + t] = acc[SPT - 1].lo.im[cc];
       }
     }
     __syncthreads();
     if (active) {
       const int cn = (chunk + 1 == nchunk) ? 0 : chunk + 1;
       const int cp = (chunk == 0) ? nchunk - 1 : chunk - 1;
-      const C fn = (chunk + 1 == nchunk) ? -mf : C(1);
-      const C fp = (chunk == 0) ? -mf : C(1);
-      roll_5d<P, true, SPT>(F, x4, s0, Ls, alpha, beta, mf, [&](int j, const C *v) {
-        C o[24];
+      const V2 fn = bc<V2>((chunk + 1 == nchunk) ? -mf : C(1));
+      const V2 fp = bc<V2>((chunk == 0) ? -mf : C(1));
+      const V2 mb = bc<V2>(C(-0.5) * b), mc = bc<V2>(C(-0.5) * c);
+      roll_5d<P, true, SPT>(F, x4, s0, Ls, alpha, beta, mf, [&](int j, const Spinor<V2> &v) {
+        Spinor<V2> o;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-          // upper: (K^+ acc)_s = acc_up(s+1)
-          C kup = (j + 1 < SPT) ? acc[(j + 1 < SPT) ? j + 1 : 0][i]
-                                : fn * sm_up[((size_t)cn * 12 + i) * tx + t];
-          // lower: (K^+ acc)_s = acc_lo(s-1)
-          C klo = (j > 0) ? acc[(j > 0) ? j - 1 : 0][12 + i]
-                          : fp * sm_lo[((size_t)cp * 12 + i) * tx + t];
-          o[i] = v[i] - C(0.5) * (b * acc[j][i] + c * kup);
-          o[12 + i] = v[12 + i] - C(0.5) * (b * acc[j][12 + i] + c * klo);
+        for (int cc = 0; cc < 3; ++cc) {
+          // upper: (K^+ acc)_s = acc_up(s+1); lower: (K^+ acc)_s = acc_lo(s-1)
+          V2 kur, kui, klr, kli;
+          if (j + 1 < SPT) {
+            kur = acc[(j + 1 < SPT) ? j + 1 : 0].up.re[cc];
+            kui = acc[(j + 1 < SPT) ? j + 1 : 0].up.im[cc];
+          } else {
+            kur = p_mul(fn, sm_up[((size_t)cn * 6 + 2 * cc) * tx + t]);
+            kui = p_mul(fn, sm_up[((size_t)cn * 6 + 2 * cc + 1) * tx + t]);
+          }
+          if (j > 0) {
+            klr = acc[(j > 0) ? j - 1 : 0].lo.re[cc];
+            kli = acc[(j > 0) ? j - 1 : 0].lo.im[cc];
+          } else {
+            klr = p_mul(fp, sm_lo[((size_t)cp * 6 + 2 * cc) * tx + t]);
+            kli = p_mul(fp, sm_lo[((size_t)cp * 6 + 2 * cc + 1) * tx + t]);
+          }
+          o.up.re[cc] = p_fma(mc, kur, p_fma(mb, acc[j].up.re[cc], v.up.re[cc]));
+          o.up.im[cc] = p_fma(mc, kui, p_fma(mb, acc[j].up.im[cc], v.up.im[cc]));
+          o.lo.re[cc] = p_fma(mc, klr, p_fma(mb, acc[j].lo.re[cc], v.lo.re[cc]));
+          o.lo.im[cc] = p_fma(mc, kli, p_fma(mb, acc[j].lo.im[cc], v.lo.im[cc]));
         }
         store(j, o);
       });
@@ -373,79 +784,122 @@ __global__ void dslash_kernel(const DslashParams p) {
   }
 }
 
-template <class P, int OP, int SPT>
+template <class P, int OP, int SPT, int VAR>
+size_t dslash_smem(int tx, int nchunk) {
+  size_t smem = 0;
+  if (VAR == 1) smem += kStages * StageLayout<P, OP == OP_D, SPT>::stage_bytes(tx * nchunk);
+  if (OP == OP_DDAG) smem += 2 * (size_t)nchunk * 12 * tx * sizeof(typename P::C);  // 6 pairs
+  return smem;
+}
+
+template <class P, int OP, int SPT, int VAR>
 int launch_one(const DslashParams &p, int tx, cudaStream_t st) {
   const int nchunk = p.Ls / SPT;
   dim3 block(tx, nchunk);
-  dim3 grid((p.V4 + tx - 1) / tx, p.nrhs);
-  size_t smem = 0;
-  if (OP == OP_DDAG) smem = 2 * (size_t)nchunk * 12 * tx * sizeof(typename P::C);
+  dim3 grid((unsigned)(((long long)p.V4 + tx - 1) / tx * p.nrhs));
+  const size_t smem = dslash_smem<P, OP, SPT, VAR>(tx, nchunk);
   // per-instantiation launch limits, queried once
   static int max_threads = 0;
   static size_t smem_set = 48 * 1024;
   if (!max_threads) {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, SPT>) != cudaSuccess) return -1;
+    if (cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, SPT, VAR>) != cudaSuccess) return -1;
     max_threads = fa.maxThreadsPerBlock;
   }
   if (tx < 32 || tx % 32 || tx * nchunk > max_threads) return -3;
+  if (smem > 227 * 1024) return -3;
   if (smem > smem_set) {
-    if (cudaFuncSetAttribute(dslash_kernel<P, OP, SPT>,
+    if (cudaFuncSetAttribute(dslash_kernel<P, OP, SPT, VAR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return -3;
     smem_set = smem;
   }
-  dslash_kernel<P, OP, SPT><<<grid, block, smem, st>>>(p);
+  dslash_kernel<P, OP, SPT, VAR><<<grid, block, smem, st>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <class P, int OP>
-int launch_op(const DslashParams &p, TileConfig cfg, cudaStream_t st) {
+template <class P, int OP, int VAR>
+int launch_spt(const DslashParams &p, TileConfig cfg, cudaStream_t st) {
   switch (cfg.spt) {
-    case 1: return launch_one<P, OP, 1>(p, cfg.tx, st);
-    case 2: return launch_one<P, OP, 2>(p, cfg.tx, st);
-    case 3: return launch_one<P, OP, 3>(p, cfg.tx, st);
-    case 4: return launch_one<P, OP, 4>(p, cfg.tx, st);
+    case 1: return launch_one<P, OP, 1, VAR>(p, cfg.tx, st);
+    case 2: return launch_one<P, OP, 2, VAR>(p, cfg.tx, st);
+    case 3: return launch_one<P, OP, 3, VAR>(p, cfg.tx, st);
+    case 4: return launch_one<P, OP, 4, VAR>(p, cfg.tx, st);
     default: return -2;
   }
 }
 
-template <class P, int OP>
-int max_threads_op(int spt) {
+template <class P, int OP, int VAR>
+int max_threads_var(int spt) {
   cudaFuncAttributes fa;
   cudaError_t e;
   switch (spt) {
-    case 1: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 1>); break;
-    case 2: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 2>); break;
-    case 3: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 3>); break;
-    case 4: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 4>); break;
+    case 1: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 1, VAR>); break;
+    case 2: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 2, VAR>); break;
+    case 3: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 3, VAR>); break;
+    case 4: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 4, VAR>); break;
     default: return 0;
   }
   return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
 }
 
-template <class P>
-int max_threads_impl(int op, int spt) {
+// Largest CTA that (op, spt) of variant VAR can launch: register limit and, for
+// the staged variant, the 227 KB shared-memory limit.
+template <class P, int OP, int VAR>
+int max_threads_op(int spt) {
+  int m = max_threads_var<P, OP, VAR>(spt);
+  if (VAR != 1) return m;
+  m -= m % 32;
+  while (m >= 32) {
+    size_t smem = 0;
+    switch (spt) {
+      case 1: smem = kStages * StageLayout<P, OP == OP_D, 1>::stage_bytes(m); break;
+      case 2: smem = kStages * StageLayout<P, OP == OP_D, 2>::stage_bytes(m); break;
+      case 3: smem = kStages * StageLayout<P, OP == OP_D, 3>::stage_bytes(m); break;
+      case 4: smem = kStages * StageLayout<P, OP == OP_D, 4>::stage_bytes(m); break;
+    }
+    if (OP == OP_DDAG) smem += (size_t)m * 24 * sizeof(typename P::C);
+    if (smem <= 227 * 1024) break;
+    m -= 32;
+  }
+  return m < 32 ? 0 : m;
+}
+
+// Entry points of one (precision, variant) translation unit.
+template <class P, int VAR>
+int launch_variant(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st) {
+  if (cfg.spt < 1 || p.Ls % cfg.spt) return -2;
   switch (op) {
-    case OP_DHOP: return max_threads_op<P, OP_DHOP>(spt);
-    case OP_DHOP_DAG: return max_threads_op<P, OP_DHOP_DAG>(spt);
-    case OP_D: return max_threads_op<P, OP_D>(spt);
-    case OP_DDAG: return max_threads_op<P, OP_DDAG>(spt);
+    case OP_DHOP: return launch_spt<P, OP_DHOP, VAR>(p, cfg, st);
+    case OP_DHOP_DAG: return launch_spt<P, OP_DHOP_DAG, VAR>(p, cfg, st);
+    case OP_D: return launch_spt<P, OP_D, VAR>(p, cfg, st);
+    case OP_DDAG: return launch_spt<P, OP_DDAG, VAR>(p, cfg, st);
+  }
+  return -2;
+}
+
+template <class P, int VAR>
+int max_threads_variant(int op, int spt) {
+  switch (op) {
+    case OP_DHOP: return max_threads_op<P, OP_DHOP, VAR>(spt);
+    case OP_DHOP_DAG: return max_threads_op<P, OP_DHOP_DAG, VAR>(spt);
+    case OP_D: return max_threads_op<P, OP_D, VAR>(spt);
+    case OP_DDAG: return max_threads_op<P, OP_DDAG, VAR>(spt);
   }
   return 0;
 }
 
-template <class P>
-int launch_dslash_impl(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st) {
-  if (cfg.spt < 1 || p.Ls % cfg.spt) return -2;
-  switch (op) {
-    case OP_DHOP: return launch_op<P, OP_DHOP>(p, cfg, st);
-    case OP_DHOP_DAG: return launch_op<P, OP_DHOP_DAG>(p, cfg, st);
-    case OP_D: return launch_op<P, OP_D>(p, cfg, st);
-    case OP_DDAG: return launch_op<P, OP_DDAG>(p, cfg, st);
-    default: return -2;
-  }
-}
-
 }  // namespace dw
+
+// One translation unit per (precision, variant) keeps the builds parallel.
+#define DW_DSLASH_INSTANTIATE(PREC, VAR)                                                  \
+  namespace dw {                                                                         \
+  int launch_dslash_##PREC##_v##VAR(const DslashParams &p, int op, TileConfig cfg,       \
+                                    cudaStream_t st) {                                   \
+    return launch_variant<PREC, VAR>(p, op, cfg, st);                                    \
+  }                                                                                      \
+  int dslash_max_threads_##PREC##_v##VAR(int op, int spt) {                              \
+    return max_threads_variant<PREC, VAR>(op, spt);                                      \
+  }                                                                                      \
+  }

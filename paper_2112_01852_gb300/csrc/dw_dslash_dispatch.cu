@@ -1,0 +1,87 @@
+// Dispatch of the stencil kernel over (precision, hop-phase variant); each
+// pair lives in its own translation unit.  FP64 builds only the register
+// variants (its arithmetic, not its loads, bounds it on this GPU).
+#include "dw_common.cuh"
+
+namespace dw {
+
+int launch_dslash_F64_v0(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F64_v0(int op, int spt);
+int launch_dslash_F64_v2(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F64_v2(int op, int spt);
+int launch_dslash_F32_v0(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F32_v0(int op, int spt);
+int launch_dslash_F32_v1(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F32_v1(int op, int spt);
+int launch_dslash_F32_v2(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F32_v2(int op, int spt);
+int launch_dslash_F32_v3(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F32_v3(int op, int spt);
+int launch_dslash_F16_v0(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F16_v0(int op, int spt);
+int launch_dslash_F16_v1(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F16_v1(int op, int spt);
+int launch_dslash_F16_v2(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F16_v2(int op, int spt);
+int launch_dslash_F16_v3(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F16_v3(int op, int spt);
+
+int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st) {
+  const int cfg_variant = cfg.variant;
+  switch (prec) {
+    case DW_F64:
+      switch (cfg_variant) {
+        case 0: return launch_dslash_F64_v0(p, op, cfg, st);
+        case 2: return launch_dslash_F64_v2(p, op, cfg, st);
+        default: return -2;
+      }
+    case DW_F32:
+      switch (cfg_variant) {
+        case 0: return launch_dslash_F32_v0(p, op, cfg, st);
+        case 1: return launch_dslash_F32_v1(p, op, cfg, st);
+        case 2: return launch_dslash_F32_v2(p, op, cfg, st);
+        case 3: return launch_dslash_F32_v3(p, op, cfg, st);
+        default: return -2;
+      }
+    case DW_F16:
+      switch (cfg_variant) {
+        case 0: return launch_dslash_F16_v0(p, op, cfg, st);
+        case 1: return launch_dslash_F16_v1(p, op, cfg, st);
+        case 2: return launch_dslash_F16_v2(p, op, cfg, st);
+        case 3: return launch_dslash_F16_v3(p, op, cfg, st);
+        default: return -2;
+      }
+  }
+  return -2;
+}
+
+int dslash_max_threads(int prec, int op, int spt, int variant) {
+  const int cfg_variant = variant;
+  switch (prec) {
+    case DW_F64:
+      switch (cfg_variant) {
+        case 0: return dslash_max_threads_F64_v0(op, spt);
+        case 2: return dslash_max_threads_F64_v2(op, spt);
+        default: return 0;
+      }
+    case DW_F32:
+      switch (cfg_variant) {
+        case 0: return dslash_max_threads_F32_v0(op, spt);
+        case 1: return dslash_max_threads_F32_v1(op, spt);
+        case 2: return dslash_max_threads_F32_v2(op, spt);
+        case 3: return dslash_max_threads_F32_v3(op, spt);
+        default: return 0;
+      }
+    case DW_F16:
+      switch (cfg_variant) {
+        case 0: return dslash_max_threads_F16_v0(op, spt);
+        case 1: return dslash_max_threads_F16_v1(op, spt);
+        case 2: return dslash_max_threads_F16_v2(op, spt);
+        case 3: return dslash_max_threads_F16_v3(op, spt);
+        default: return 0;
+      }
+  }
+  return 0;
+}
+
+}  // namespace dw

@@ -6,8 +6,15 @@ namespace dw {
 
 // ---------------------------------------------------------------------------
 // Canonical fermion complex128 [rhs][x4][s][spin][col] <-> internal planes.
-// One thread per (x4, s) of one RHS; the 24 reals of the site map to the
-// internal reals in the same order (upper spins first).
+// One thread per (x4, s) of one RHS.  Internal real I = half*12 + c*4 + ri*2 + j
+// (chirality half, colour c, re/im ri, spin j within the half) holds the
+// canonical real ((2*half + j)*3 + c)*2 + ri: each 4-real quad is the spin
+// pair (Re j0, Re j1, Im j0, Im j1) of one colour.
+__device__ __forceinline__ int canon_real(int I) {
+  const int half = I / 12, i = I % 12;
+  const int c = i / 4, ri = (i % 4) / 2, j = i % 2;
+  return ((2 * half + j) * 3 + c) * 2 + ri;
+}
 template <class P>
 __global__ void pack_kernel(typename P::vec *dst, const double *src, long long V5, int V4,
                             int Ls, long long plane, long long rhs_stride) {
@@ -23,7 +30,7 @@ __global__ void pack_kernel(typename P::vec *dst, const double *src, long long V
   for (int q = 0; q < NP; ++q) {
     double r[P::R];
 #pragma unroll
-    for (int k = 0; k < P::R; ++k) r[k] = p[q * P::R + k];
+    for (int k = 0; k < P::R; ++k) r[k] = p[canon_real(q * P::R + k)];
     d[q * plane] = narrow_from_f64(r, (typename P::vec *)nullptr);
   }
 }
@@ -45,7 +52,7 @@ __global__ void unpack_kernel(double *dst, const typename P::vec *src, long long
     C r[P::R];
     load_vec<P>(r, sp + q * plane);
 #pragma unroll
-    for (int k = 0; k < P::R; ++k) p[q * P::R + k] = (double)r[k];
+    for (int k = 0; k < P::R; ++k) p[canon_real(q * P::R + k)] = (double)r[k];
   }
 }
 

@@ -25,9 +25,10 @@ int tune_tile(dw_lattice *lat, int op, int nrhs, cudaStream_t st) {
   float best = 1e30f;
   TileConfig best_t = default_tile(lat, prec, op, nrhs);
   const int reps = 5;
+  for (int variant = 0; variant < kNumVariants; ++variant)
   for (int spt : {1, 2, 3, 4}) {
     for (int tx : {32, 64, 128, 256}) {
-      TileConfig t{spt, tx};
+      TileConfig t{spt, tx, variant};
       if (!tile_valid(lat, prec, op, t)) continue;
       // warm-up launch doubles as the validity check
       if (run_dslash(lat, prec, op, lat->stage_out, lat->stage_in, mf.data(), nrhs, st, &t)) {

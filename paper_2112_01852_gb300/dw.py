@@ -101,8 +101,8 @@ def load_library():
             "dw_apply_DdagD": (I, [P, P, P, DP, I, P]),
             "dw_apply_host": (I, [P, I, P, P, DP, I, P]),
             "dw_cg_solve": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
-            "dw_set_tile": (I, [P, I, I, I, I, I]),
-            "dw_tune": (I, [P, I, I, IP, IP, P]),
+            "dw_set_tile": (I, [P, I, I, I, I, I, I]),
+            "dw_tune": (I, [P, I, I, IP, IP, IP, P]),
             "dw_fermion_bytes": (S, [P, I, I]),
             "dw_pack_fermion": (I, [P, P, I, P, I, P]),
             "dw_unpack_fermion": (I, [P, P, P, I, I, P]),
@@ -191,17 +191,19 @@ def dw_cg_solve(lat, x, b, mf, nrhs, tol, maxit, mode, stream=0):
     return rc, list(stats)
 
 
-def dw_set_tile(lat, op, prec, nrhs, spt, tx):
-    _check(load_library().dw_set_tile(lat, int(op), int(prec), int(nrhs), int(spt), int(tx)))
+def dw_set_tile(lat, op, prec, nrhs, spt, tx, variant=0):
+    _check(load_library().dw_set_tile(lat, int(op), int(prec), int(nrhs), int(spt), int(tx),
+                                      int(variant)))
 
 
 def dw_tune(lat, op, nrhs, stream=0):
-    """Returns the chosen (spt, tx)."""
+    """Returns the chosen (spt, tx, variant)."""
     spt = ctypes.c_int()
     tx = ctypes.c_int()
+    var = ctypes.c_int()
     _check(load_library().dw_tune(lat, int(op), int(nrhs), ctypes.byref(spt), ctypes.byref(tx),
-                                  stream))
-    return spt.value, tx.value
+                                  ctypes.byref(var), stream))
+    return spt.value, tx.value, var.value
 
 
 def dw_fermion_bytes(lat, prec, nrhs):

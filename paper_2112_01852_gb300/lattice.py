@@ -109,8 +109,9 @@ class Lattice:
         dw.dw_apply_host(self.handle, op, out_host.data_ptr(), in_host.data_ptr(),
                          None if mf is None else _masses(mf, nrhs), nrhs, _stream())
 
-    def set_tile(self, op, spt, tx, nrhs=0, prec=None):
-        dw.dw_set_tile(self.handle, op, self.prec if prec is None else prec, nrhs, spt, tx)
+    def set_tile(self, op, spt, tx, variant=0, nrhs=0, prec=None):
+        dw.dw_set_tile(self.handle, op, self.prec if prec is None else prec, nrhs, spt, tx,
+                       variant)
 
     def tune(self, op, nrhs=1):
         return dw.dw_tune(self.handle, op, nrhs, _stream())

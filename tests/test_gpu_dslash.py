@@ -81,19 +81,21 @@ def test_all_tiles_ragged(Ls):
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F64, M5=1.6, b=1.25, c=0.75, bc=bc)
     lat.load_gauge(U)
     refs = {op: run_oracle(op, psi, U, dims, Ls, 1.6, 1.25, 0.75, mfs, bc) for op in STENCIL_OPS}
-    ran = 0
-    for spt, tx in valid_tiles(Ls):
-        for op in STENCIL_OPS:
-            try:
-                lat.set_tile(op, spt, tx)
-            except dw.DWError as e:  # CTA beyond this kernel's register budget
-                assert e.code == dw.DW_ERR_ARG
-                continue
-            ran += 1
-            got = run_gpu(lat, op, psi, mf=mfs)
-            err = max_rel(got, refs[op])
-            assert err <= TOL[dw.DW_F64], (OP_NAMES[op], spt, tx, err)
-    assert ran >= len(STENCIL_OPS) * len([t for t in valid_tiles(Ls) if t[1] == 32])
+    ran = set()
+    for variant in range(4):
+        for spt, tx in valid_tiles(Ls):
+            for op in STENCIL_OPS:
+                try:
+                    lat.set_tile(op, spt, tx, variant)
+                except dw.DWError as e:  # variant not built at FP64, or CTA too large
+                    assert e.code == dw.DW_ERR_ARG
+                    continue
+                ran.add((variant, op))
+                got = run_gpu(lat, op, psi, mf=mfs)
+                err = max_rel(got, refs[op])
+                assert err <= TOL[dw.DW_F64], (OP_NAMES[op], spt, tx, variant, err)
+    # FP64 builds the register variants 0 and 2; each ran for every operator
+    assert {(v, op) for v in (0, 2) for op in STENCIL_OPS} <= ran
     lat.close()
 
 
@@ -107,6 +109,29 @@ def test_two_site_lattice_sums_coinciding_neighbours():
         got = run_gpu(lat, op, psi, mf=[0.05])
         ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.05])
         assert max_rel(got, ref) <= TOL[dw.DW_F64], OP_NAMES[op]
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [dw.DW_F32, dw.DW_F16], ids=["f32", "f16"])
+def test_both_variants_low_precision(prec):
+    dims, Ls = (8, 4, 6, 10), 12
+    U, psi = make_case(dims, Ls, 2, seed=15)
+    mfs = [0.01, 0.04]
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
+    lat.load_gauge(U)
+    refs = {op: run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mfs) for op in STENCIL_OPS}
+    ran = set()
+    for variant in range(4):
+        for spt in (1, 2, 3, 4):
+            for op in STENCIL_OPS:
+                try:
+                    lat.set_tile(op, spt, 32, variant)
+                except dw.DWError:
+                    continue
+                ran.add((variant, op))
+                got = run_gpu(lat, op, psi, mf=mfs)
+                assert max_rel(got, refs[op]) <= TOL[prec], (OP_NAMES[op], spt, variant)
+    assert {(v, op) for v in range(4) for op in STENCIL_OPS} <= ran
     lat.close()
 
 
@@ -202,8 +227,9 @@ def test_tune_picks_valid_tile_and_stays_exact():
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
     lat.load_gauge(U)
     for op in STENCIL_OPS:
-        spt, tx = lat.tune(op, 1)
+        spt, tx, variant = lat.tune(op, 1)
         assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
+        assert variant in range(4)
         got = run_gpu(lat, op, psi, mf=[0.01])
         ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
         assert max_rel(got, ref) <= TOL[dw.DW_F32], OP_NAMES[op]
@@ -247,6 +273,9 @@ def test_argument_errors():
     assert e.value.code == dw.DW_ERR_ARG
     with pytest.raises(dw.DWError) as e:
         lat.set_tile(dw.DW_OP_DHOP, 1, 48)  # not a multiple of 32
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        lat.set_tile(dw.DW_OP_DHOP, 1, 32, variant=5)
     assert e.value.code == dw.DW_ERR_ARG
     assert "multiple" in dw.dw_last_error() or "invalid" in dw.dw_last_error()
     torch.cuda.synchronize()
