@@ -121,6 +121,25 @@ int dw_apply_DdagD(dw_lattice *lat, void *out, const void *in, const double *mf,
                    void *stream);
 
 /*
+ * out = D^+ D in, like dw_apply_DdagD, without allocating anything.  The paper
+ * has no counterpart: this entry point serves callers that cannot let the
+ * library call cudaMalloc (for example a process whose device memory is all
+ * handed out by its own pool allocator).  The intermediate D in is kept in one
+ * fixed 32 MiB array compiled into the library, which every GPU that loads the
+ * library holds until the process exits; the call makes no allocation call of
+ * any kind.  nrhs * dw_fermion_bytes(lat, prec, 1) above 32 MiB is rejected with
+ * DW_ERR_ARG before anything is launched.  The current device must be the
+ * lattice's.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (different streams, or different lattices on
+ * one device) race.  The D pass overwrites the whole intermediate, so nothing
+ * has to be cleared between calls.
+ */
+int dw_apply_DdagD_noalloc(dw_lattice *lat, void *out, const void *in, const double *mf,
+                           int nrhs, void *stream);
+
+/*
  * Apply operator `op` (DW_OP_*) with HOST buffers in the internal layout at
  * the lattice precision: copies in to the device, applies, copies out back and
  * synchronises the stream.  Device staging buffers are lattice-owned.

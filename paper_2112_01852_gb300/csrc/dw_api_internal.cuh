@@ -25,6 +25,9 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const int *gate = nullptr, int gate_stride = 0);
 int apply_op(dw_lattice *lat, int op, void *out, const void *in, const double *mf, int nrhs,
              cudaStream_t st);
+// Argument checks shared by the dw_apply_* entry points.
+int check_apply(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                bool need_mf);
 void cg_release(dw_lattice *lat);
 
 }  // namespace dw

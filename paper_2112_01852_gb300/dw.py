@@ -50,7 +50,8 @@ _ERRNAMES = {
 # Every symbol include/dw.h declares.
 SYMBOLS = (
     "dw_create_lattice", "dw_destroy_lattice", "dw_load_gauge", "dw_apply_Dhop",
-    "dw_apply_Dhop_dag", "dw_apply_D", "dw_apply_Ddag", "dw_apply_DdagD", "dw_apply_host",
+    "dw_apply_Dhop_dag", "dw_apply_D", "dw_apply_Ddag", "dw_apply_DdagD",
+    "dw_apply_DdagD_noalloc", "dw_apply_host",
     "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_fermion_bytes", "dw_pack_fermion",
     "dw_unpack_fermion", "dw_last_error",
 )
@@ -99,6 +100,7 @@ def load_library():
             "dw_apply_D": (I, [P, P, P, DP, I, P]),
             "dw_apply_Ddag": (I, [P, P, P, DP, I, P]),
             "dw_apply_DdagD": (I, [P, P, P, DP, I, P]),
+            "dw_apply_DdagD_noalloc": (I, [P, P, P, DP, I, P]),
             "dw_apply_host": (I, [P, I, P, P, DP, I, P]),
             "dw_cg_solve": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
             "dw_set_tile": (I, [P, I, I, I, I, I, I]),
@@ -175,6 +177,10 @@ def dw_apply_Ddag(lat, out, inp, mf, nrhs, stream=0):
 
 def dw_apply_DdagD(lat, out, inp, mf, nrhs, stream=0):
     _check(load_library().dw_apply_DdagD(lat, out, inp, _doubles(mf), int(nrhs), stream))
+
+
+def dw_apply_DdagD_noalloc(lat, out, inp, mf, nrhs, stream=0):
+    _check(load_library().dw_apply_DdagD_noalloc(lat, out, inp, _doubles(mf), int(nrhs), stream))
 
 
 def dw_apply_host(lat, op, out_host, in_host, mf, nrhs, stream=0):
