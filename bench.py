@@ -334,7 +334,7 @@ def main():
     ap.add_argument("--main-only", action="store_true",
                     help="time only the FP32 Dhop (no other operators, e2e, CG or CPU leg)")
     ap.add_argument("--tile", default=None,
-                    help="spt,tx[,variant]: fixed Dhop tile instead of tuning")
+                    help="spt,tx[,variant[,zblk]]: fixed Dhop tile instead of tuning")
     ap.add_argument("--no-cg", action="store_true")
     args = ap.parse_args()
     global DIMS, LS
@@ -372,10 +372,10 @@ def main():
     y = lat.empty(1)
     tiles = {}
     if args.tile:
-        tv = [int(v) for v in args.tile.split(",")]
-        spt, tx, var = tv[0], tv[1], (tv[2] if len(tv) > 2 else 0)
-        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var)
-        tiles[dw.DW_OP_DHOP] = (spt, tx, var)
+        tv = [int(v) for v in args.tile.split(",")] + [0, 0]
+        spt, tx, var, zb = tv[0], tv[1], tv[2], tv[3]
+        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var, zblk=zb)
+        tiles[dw.DW_OP_DHOP] = (spt, tx, var, zb)
     else:
         tiles[dw.DW_OP_DHOP] = lat.tune(dw.DW_OP_DHOP, 1)
     if not args.main_only:

@@ -171,13 +171,16 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
                 double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
 
 /*
- * Stencil-kernel tiles.  A tile is (spt, tx, variant): spt fifth-dimension
+ * Stencil-kernel tiles.  A tile is (spt, tx, variant, zblk): spt fifth-dimension
  * slices per thread (1..4, dividing Ls), tx 4D sites per CTA (a multiple of
- * 32) and the load variant of the hop phase: 0 = neighbour spinors and links
- * loaded straight into registers, direction by direction; 1 = copied one
- * direction ahead into shared memory with cp.async; 2, 3 = loaded one
- * (direction, slice) step ahead into registers, visiting t,z,y,x (2) or
- * x,y,z,t (3).  A CTA holds all Ls/spt slice groups of its tx sites.
+ * 32, taken from one (x, y) plane), the load variant of the hop phase (0 =
+ * neighbour spinors and links loaded straight into registers, direction by
+ * direction; 1 = copied one direction ahead into shared memory with cp.async;
+ * 2, 3 = loaded one (direction, slice) step ahead into registers, visiting
+ * t,z,y,x (2) or x,y,z,t (3)), and zblk, the number of z-blocks of the CTA
+ * traversal order (planes are visited block by block, t inside a block; zblk
+ * divides Lz; 0 in dw_set_tile = automatic).  A CTA holds all Ls/spt slice
+ * groups of its tx sites.
  *
  * dw_set_tile pins the tile used for operator `op` (DW_OP_DHOP .. DW_OP_DDAG)
  * at precision `prec` for launches of `nrhs` right-hand sides (0 = any count
@@ -186,11 +189,40 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
  * dw_tune times every valid tile for (op, nrhs) at the lattice precision on
  * lattice-owned scratch fields (CUDA events on `stream`, median of a few
  * launches), keeps the fastest for later calls and returns it in *spt, *tx,
- * *variant (any may be NULL).  Requires a loaded gauge field; synchronises; must not
- * be called while `stream` is being captured into a graph.
+ * *variant, *zblk (any may be NULL).  Requires a loaded gauge field;
+ * synchronises; must not be called while `stream` is being captured into a
+ * graph.
  */
-int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant);
-int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, void *stream);
+int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant,
+                int zblk);
+int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, int *zblk,
+            void *stream);
+
+/*
+ * Domain decomposition along t on one device ("virtual ranks").  The hopping
+ * term has one exchange step when the lattice is split into ranks along t
+ * (an exchange of spin-projected half spinors across the cut).  A rank owns a
+ * sub-lattice created with dims {Lx, Ly, Lz, Lt / R}, the global links of its
+ * t-range, and bc[3] = the global t sign for the last rank and +1 for the
+ * others (so the sign sits on the one link that crosses the global edge).
+ *
+ * dw_halo_pack fills the two half-spinor faces a rank sends, each
+ * dw_halo_bytes(lat, prec, nrhs) long, layout [rhs][quad 3][s][face site]:
+ *   send_dn -> the rank below: the forward-hop projection of the first t slice;
+ *   send_up -> the rank above: U_t^+ times the backward-hop projection of the
+ *              last t slice.
+ * dag selects Dhop^+ (the sign of the projections).
+ * dw_apply_Dhop_halo is dw_apply_Dhop (dw_apply_Dhop_dag for dag = 1) on the
+ * sub-lattice, with the t-neighbours of its t faces taken from recv_up (the
+ * rank above's send_dn) and recv_dn (the rank below's send_up).  It runs the
+ * same arithmetic in the same order as the undecomposed kernel with a
+ * variant-0 tile, so the stitched result equals it bit for bit.
+ */
+size_t dw_halo_bytes(const dw_lattice *lat, int prec, int nrhs);
+int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, int nrhs,
+                 int dag, void *stream);
+int dw_apply_Dhop_halo(dw_lattice *lat, void *out, const void *in, const void *recv_up,
+                       const void *recv_dn, int nrhs, int dag, void *stream);
 
 /* Bytes of one internal-layout field of nrhs right-hand sides at precision prec. */
 size_t dw_fermion_bytes(const dw_lattice *lat, int prec, int nrhs);

@@ -59,12 +59,23 @@ int ensure_buffer(void **buf, size_t *cap, size_t need) {
   return DW_OK;
 }
 
+// z-blocks of the traversal order: the fewest that keep the t-reuse window of
+// the input (2 * Lz/zblk planes x Ls slices) within ~40 MB of L2.
+int auto_zblk(const dw_lattice *lat, int prec) {
+  const double plane = (double)lat->dims[0] * lat->dims[1] * lat->Ls * 24.0 * prec_real_bytes(prec);
+  for (int z = 1; z <= lat->dims[2]; ++z) {
+    if (lat->dims[2] % z) continue;
+    if (2.0 * (lat->dims[2] / z) * plane <= 40.0e6) return z;
+  }
+  return lat->dims[2];
+}
+
 // Untuned choice: the smallest slices-per-thread whose CTA of 32 sites x Ls/spt
 // slice groups fits the kernel's register budget, then up to 256 threads.
 TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs) {
   (void)nrhs;
   const int Ls = lat->Ls;
-  TileConfig t{0, 32, 0};
+  TileConfig t{0, 32, 0, auto_zblk(lat, prec)};
   int maxt = 0;
   for (int spt : {1, 2, 3, 4}) {
     if (Ls % spt) continue;
@@ -96,15 +107,22 @@ bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (t.spt < 1 || t.spt > 4 || lat->Ls % t.spt) return false;
   if (t.tx < 32 || t.tx % 32) return false;
   if (t.variant < 0 || t.variant > kNumVariants - 1) return false;
+  if (t.zblk < 1 || lat->dims[2] % t.zblk) return false;
   const long long threads = (long long)t.tx * (lat->Ls / t.spt);
   return threads <= 1024 && threads <= dslash_max_threads(prec, op, t.spt, t.variant);
 }
 
 // Stencil launch over all RHS, in groups of at most kMaxRhsPerLaunch.
+size_t halo_bytes(const dw_lattice *lat, int prec, int nrhs) {
+  return (size_t)12 * lat->Ls * ((size_t)lat->dims[0] * lat->dims[1] * lat->dims[2]) *
+         prec_real_bytes(prec) * (size_t)nrhs;
+}
+
 int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
-               const int *gate, int gate_stride) {
+               const int *gate, int gate_stride, const void *halo_up, const void *halo_dn) {
   const size_t rhs_bytes = field_bytes(lat, prec, 1);
+  const size_t hrhs_bytes = halo_bytes(lat, prec, 1);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
     const int n = (nrhs - r0) < kMaxRhsPerLaunch ? (nrhs - r0) : kMaxRhsPerLaunch;
     DslashParams p;
@@ -121,6 +139,8 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.nrhs = n;
     p.gate = gate ? gate + (size_t)r0 * gate_stride : nullptr;
     p.gate_stride = gate_stride;
+    p.halo_up = halo_up ? (const char *)halo_up + (size_t)r0 * hrhs_bytes : nullptr;
+    p.halo_dn = halo_dn ? (const char *)halo_dn + (size_t)r0 * hrhs_bytes : nullptr;
     p.M5 = lat->M5;
     p.b = lat->b;
     p.c = lat->c;
@@ -128,8 +148,8 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     const TileConfig cfg = force ? *force : pick_tile(lat, prec, op, nrhs);
     const int rc = launch_dslash(p, prec, op, cfg, st);
     if (rc == -2)
-      return fail(DW_ERR_ARG, "unsupported tile (spt=%d, tx=%d, variant=%d) for Ls=%d", cfg.spt,
-                  cfg.tx, cfg.variant, lat->Ls);
+      return fail(DW_ERR_ARG, "unsupported tile (spt=%d, tx=%d, variant=%d, zblk=%d) for Ls=%d",
+                  cfg.spt, cfg.tx, cfg.variant, cfg.zblk, lat->Ls);
     if (rc == -3)
       return fail(DW_ERR_ARG,
                   "tile (spt=%d, tx=%d, variant=%d) exceeds the kernel's CTA limits", cfg.spt,
@@ -329,23 +349,26 @@ int dw_apply_host(dw_lattice *lat, int op, void *out_host, const void *in_host, 
   return DW_OK;
 }
 
-int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant) {
+int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant,
+                int zblk) {
   clear_error();
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
   if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
   if (prec < DW_F64 || prec > DW_F16) return fail(DW_ERR_ARG, "unknown precision %d", prec);
   if (nrhs < 0) return fail(DW_ERR_ARG, "nrhs must be >= 0");
-  TileConfig t{spt, tx, variant};
+  TileConfig t{spt, tx, variant, zblk == 0 ? auto_zblk(lat, prec) : zblk};
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
-                "invalid tile spt=%d tx=%d variant=%d for Ls=%d (slices per thread must divide "
-                "Ls, tx a multiple of 32, variant 0..3, CTA within the kernel's limits)",
-                spt, tx, variant, lat->Ls);
+                "invalid tile spt=%d tx=%d variant=%d zblk=%d for Ls=%d Lz=%d (slices per thread "
+                "must divide Ls, tx a multiple of 32, variant 0..3, zblk dividing Lz, CTA within "
+                "the kernel's limits)",
+                spt, tx, variant, zblk, lat->Ls, lat->dims[2]);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;
   return DW_OK;
 }
 
-int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, void *stream) {
+int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, int *zblk,
+            void *stream) {
   clear_error();
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
   if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
@@ -355,13 +378,63 @@ int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, 
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
     return fail(DW_ERR_STATE, "dw_tune called on a capturing stream");
-  int rc = tune_tile(lat, op, nrhs, st);
+  int rc = tune_tile(lat, lat->prec, op, nrhs, st);
   if (rc) return rc;
   const TileConfig t = pick_tile(lat, lat->prec, op, nrhs);
   if (spt) *spt = t.spt;
   if (tx) *tx = t.tx;
   if (variant) *variant = t.variant;
+  if (zblk) *zblk = t.zblk;
   return DW_OK;
+}
+
+size_t dw_halo_bytes(const dw_lattice *lat, int prec, int nrhs) {
+  if (!lat || nrhs < 0 || prec < DW_F64 || prec > DW_F16) return 0;
+  return halo_bytes(lat, prec, nrhs);
+}
+
+int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, int nrhs,
+                 int dag, void *stream) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!send_dn || !send_up || !in) return fail(DW_ERR_ARG, "buffer pointer is NULL");
+  if (!aligned16(send_dn) || !aligned16(send_up) || !aligned16(in))
+    return fail(DW_ERR_ARG, "buffers must be 16-byte aligned");
+  if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
+  if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  DslashParams p;
+  memset(&p, 0, sizeof(p));
+  p.in = in;
+  p.gmain = lat->gmain[lat->prec];
+  p.gtail = lat->gtail[lat->prec];
+  for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
+  p.V4 = (int)lat->V4;
+  p.Ls = lat->Ls;
+  p.plane = lat->V5;
+  p.rhs_stride = lat->V5 * (24 / prec_reals_per_vec(lat->prec));
+  p.nrhs = nrhs;
+  int rc;
+  switch (lat->prec) {
+    case DW_F64: rc = launch_halo_pack_F64(p, send_dn, send_up, dag, (cudaStream_t)stream); break;
+    case DW_F32: rc = launch_halo_pack_F32(p, send_dn, send_up, dag, (cudaStream_t)stream); break;
+    default: rc = launch_halo_pack_F16(p, send_dn, send_up, dag, (cudaStream_t)stream); break;
+  }
+  if (rc) return cuda_fail(cudaGetLastError(), "halo pack launch");
+  return DW_OK;
+}
+
+int dw_apply_Dhop_halo(dw_lattice *lat, void *out, const void *in, const void *recv_up,
+                       const void *recv_dn, int nrhs, int dag, void *stream) {
+  clear_error();
+  int rc = check_apply(lat, out, in, nullptr, nrhs, false);
+  if (rc) return rc;
+  if (!recv_up || !recv_dn) return fail(DW_ERR_ARG, "halo pointer is NULL");
+  if (!aligned16(recv_up) || !aligned16(recv_dn))
+    return fail(DW_ERR_ARG, "halos must be 16-byte aligned");
+  const int op = dag ? OP_DHOP_DAG : OP_DHOP;
+  TileConfig t = default_tile(lat, lat->prec, op, nrhs);  // the halo path is variant 0
+  return run_dslash(lat, lat->prec, op, out, in, nullptr, nrhs, (cudaStream_t)stream, &t,
+                    nullptr, 0, recv_up, recv_dn);
 }
 
 size_t dw_fermion_bytes(const dw_lattice *lat, int prec, int nrhs) {

@@ -13,16 +13,22 @@ size_t field_bytes(const dw_lattice *lat, int prec, int nrhs);
 FieldGeom geom(const dw_lattice *lat);
 int ensure_buffer(void **buf, size_t *cap, size_t need);
 TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs);
+int auto_zblk(const dw_lattice *lat, int prec);
 TileConfig pick_tile(dw_lattice *lat, int prec, int op, int nrhs);
 bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t);
-// Time all valid tiles for (op, nrhs) at the lattice precision; store the best.
-int tune_tile(dw_lattice *lat, int op, int nrhs, cudaStream_t st);
+// Time the valid tiles for (op, nrhs) at precision `prec` and store the best
+// (quick: only tx <= 64 and the automatic z-blocking).
+int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool quick = false);
 // Stencil launch (op = OpKind) at precision `prec` over nrhs RHS; mf_host may be
 // NULL for the hopping-only kinds; `force` overrides the tile choice.
-// `gate` (optional) skips the CTAs of RHS r unless gate[r * gate_stride] != 0.
+// `gate` (optional) skips the CTAs of RHS r unless gate[r * gate_stride] != 0;
+// halo_up / halo_dn (optional, variant 0 tiles only) replace the t-neighbours
+// at the t faces of a decomposed sub-lattice.
 int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
-               const int *gate = nullptr, int gate_stride = 0);
+               const int *gate = nullptr, int gate_stride = 0, const void *halo_up = nullptr,
+               const void *halo_dn = nullptr);
+size_t halo_bytes(const dw_lattice *lat, int prec, int nrhs);
 int apply_op(dw_lattice *lat, int op, void *out, const void *in, const double *mf, int nrhs,
              cudaStream_t st);
 // Argument checks shared by the dw_apply_* entry points.

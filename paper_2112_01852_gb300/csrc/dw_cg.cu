@@ -195,6 +195,14 @@ extern "C" int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double
       cudaMemsetAsync(w->xs, 0, fpr, st) != cudaSuccess)
     return cuda_fail(cudaGetLastError(), "solver setup");
 
+  // tile choice for the inner operator of this solve (timed once per lattice
+  // and RHS count, then cached; the FP64 operator of the reliable updates keeps
+  // the untuned tile unless it is the inner operator)
+  for (int op : {(int)OP_D, (int)OP_DDAG})
+    if (!lat->tuned.count(std::make_tuple(S.pp, op, nrhs)) &&
+        (rc = tune_tile(lat, S.pp, op, nrhs, st, true)))
+      return rc;
+
   // initial residual
   if ((rc = S.reliable(x, b, 1))) return rc;
 

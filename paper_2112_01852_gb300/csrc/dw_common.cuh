@@ -161,6 +161,10 @@ struct DslashParams {
   int nrhs;             // right-hand sides in this launch (<= kMaxRhsPerLaunch)
   const int *gate;      // optional: CTAs of RHS r run only if gate[r * gate_stride] != 0
   int gate_stride;
+  const void *halo_up;  // optional t-face halves from the rank above (variant 0 only)
+  const void *halo_dn;  // optional t-face halves from the rank below (variant 0 only)
+  int tiles_per_plane;  // set by the launcher: CTAs per (x, y) plane
+  int zblk;             // set by the launcher: z-blocks of the traversal order
   double M5, b, c;
   double mf[64];         // per-RHS masses, passed by value
 };
@@ -172,6 +176,7 @@ struct TileConfig {
   int spt;      // fifth-dimension slices per thread
   int tx;       // 4D sites per CTA (multiple of 32)
   int variant;  // hop-phase load scheme, 0 .. kNumVariants-1 (see dw.h)
+  int zblk;     // z-blocks of the CTA traversal order (divides Lz)
 };
 constexpr int kNumVariants = 4;
 
@@ -181,6 +186,13 @@ constexpr int kNumVariants = 4;
 int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
 // Largest CTA the stencil kernel (op, spt, variant) can launch (0: none).
 int dslash_max_threads(int prec, int op, int spt, int variant);
+// Face halves of a t-decomposed sub-lattice (see dw_halo_pack).
+int launch_halo_pack_F64(const DslashParams &p, void *send_dn, void *send_up, int dag,
+                         cudaStream_t st);
+int launch_halo_pack_F32(const DslashParams &p, void *send_dn, void *send_up, int dag,
+                         cudaStream_t st);
+int launch_halo_pack_F16(const DslashParams &p, void *send_dn, void *send_up, int dag,
+                         cudaStream_t st);
 
 struct CGWork;
 

@@ -199,8 +199,11 @@ __device__ __forceinline__ void quad_in(double2 &re, double2 &im, const double2 
   re = __ldg(p);
   im = __ldg(p + plane);
 }
+// Outputs are written once and not re-read by the kernel: streaming stores
+// (evict-first) keep them from displacing neighbour spinors that are still to
+// be reused from L2.
 __device__ __forceinline__ void quad_out(float4 *p, long long, float2 re, float2 im) {
-  *p = make_float4(re.x, re.y, im.x, im.y);
+  __stcs(p, make_float4(re.x, re.y, im.x, im.y));
 }
 __device__ __forceinline__ void quad_out(uint2 *p, long long, float2 re, float2 im) {
   __half2 a = __float22half2_rn(re);
@@ -208,11 +211,11 @@ __device__ __forceinline__ void quad_out(uint2 *p, long long, float2 re, float2 
   uint2 v;
   v.x = *reinterpret_cast<unsigned int *>(&a);
   v.y = *reinterpret_cast<unsigned int *>(&b);
-  *p = v;
+  __stcs(p, v);
 }
 __device__ __forceinline__ void quad_out(double2 *p, long long plane, double2 re, double2 im) {
-  p[0] = re;
-  p[plane] = im;
+  __stcs(p, re);
+  __stcs(p + plane, im);
 }
 
 template <class P>
@@ -605,6 +608,126 @@ __device__ __forceinline__ void hop_prefetch(Spinor<typename Pair<P>::type> (&ac
   }
 }
 
+// ---------------------------------------------------------------------------
+// Domain decomposition along t ("virtual ranks").  A sub-lattice that owns a
+// t-range of the global lattice does not see its t-neighbour spinors; at its
+// t faces it uses half spinors received from the neighbouring ranks instead:
+//   up   (from the rank above): h = (projection of the forward t hop) of the
+//        neighbour's spinor at its first t slice; this rank applies its own
+//        link U_t(x) and reconstructs;
+//   down (from the rank below): w = U_t(x - t)^+ times the projection of the
+//        backward hop, computed by its owner with its own link.
+// Both are made by the same project / su3_mul code the single-domain kernel
+// runs, so the decomposed result equals the single-domain one bit for bit.
+// Halo layout per RHS: 3 quads x Ls x (Lx Ly Lz) face sites, [quad][s][face].
+template <class P, int S, bool FIRST, int SPT>
+__device__ __forceinline__ void halo_hop_up(Spinor<typename Pair<P>::type> (&acc)[SPT],
+                                            const typename P::vec *halo, long long hplane,
+                                            int Vf, int face, const typename P::vec *gmain,
+                                            const typename P::tvec *gtail, int x4, int V4,
+                                            int s0) {
+  using C = typename P::C;
+  using V2 = typename Pair<P>::type;
+  constexpr int VPQ = 4 / P::R;
+  C U[18];
+  load_link<P>(U, gmain, gtail, 3, x4, V4);
+#pragma unroll
+  for (int j = 0; j < SPT; ++j) {
+    Half<V2> h, w;
+    const typename P::vec *b = halo + (long long)(s0 + j) * Vf + face;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) quad_in(h.re[c], h.im[c], b + (long long)c * VPQ * hplane, hplane);
+    su3_mul<false>(w, U, h);
+    reconstruct<3, S, FIRST>(acc[j], w);
+  }
+}
+
+template <class P, int S, int SPT>
+__device__ __forceinline__ void halo_hop_down(Spinor<typename Pair<P>::type> (&acc)[SPT],
+                                              const typename P::vec *halo, long long hplane,
+                                              int Vf, int face, int s0) {
+  using V2 = typename Pair<P>::type;
+  constexpr int VPQ = 4 / P::R;
+#pragma unroll
+  for (int j = 0; j < SPT; ++j) {
+    Half<V2> w;
+    const typename P::vec *b = halo + (long long)(s0 + j) * Vf + face;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) quad_in(w.re[c], w.im[c], b + (long long)c * VPQ * hplane, hplane);
+    reconstruct<3, S, false>(acc[j], w);
+  }
+}
+
+// Face halves a rank sends: to the rank below, the forward-hop projection of
+// its first t slice; to the rank above, U_t^+ times the backward-hop
+// projection of its last t slice.  One thread per (face site, s) of one RHS.
+template <class P, bool DAG>
+__global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send_up,
+                                 const typename P::vec *in, const typename P::vec *gmain,
+                                 const typename P::tvec *gtail, int V4, int Vf, int Lt, int Ls,
+                                 long long plane, long long rhs_stride, long long hplane,
+                                 long long hrhs) {
+  using C = typename P::C;
+  using V2 = typename Pair<P>::type;
+  constexpr int SF = DAG ? 1 : -1;
+  constexpr int SB = -SF;
+  constexpr int VPQ = 4 / P::R;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (i >= (long long)Vf * Ls) return;
+  const int face = (int)(i % Vf);
+  const int s = (int)(i / Vf);
+  Field<P> F;
+  F.base = in + (long long)rhs * rhs_stride;
+  F.plane = plane;
+  F.V4 = V4;
+  {  // first slice -> rank below
+    Spinor<V2> v;
+    F.load_half(v.up, face, s, 0);
+    F.load_half(v.lo, face, s, 1);
+    Half<V2> h;
+    project<3, SF>(h, v.up, v.lo);
+    typename P::vec *o = send_dn + (long long)rhs * hrhs + (long long)s * Vf + face;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) quad_out(o + (long long)c * VPQ * hplane, hplane, h.re[c], h.im[c]);
+  }
+  {  // last slice -> rank above
+    const int x4 = face + (Lt - 1) * Vf;
+    Spinor<V2> v;
+    F.load_half(v.up, x4, s, 0);
+    F.load_half(v.lo, x4, s, 1);
+    Half<V2> h, w;
+    project<3, SB>(h, v.up, v.lo);
+    C U[18];
+    load_link<P>(U, gmain, gtail, 3, x4, V4);
+    su3_mul<true>(w, U, h);
+    typename P::vec *o = send_up + (long long)rhs * hrhs + (long long)s * Vf + face;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) quad_out(o + (long long)c * VPQ * hplane, hplane, w.re[c], w.im[c]);
+  }
+}
+
+template <class P>
+int launch_halo_pack_impl(const DslashParams &p, void *send_dn, void *send_up, int dag,
+                          cudaStream_t st) {
+  const int Vf = p.L[0] * p.L[1] * p.L[2];
+  const long long hplane = (long long)p.Ls * Vf;
+  const long long hrhs = hplane * (12 / P::R);
+  const int tpb = 128;
+  dim3 grid((unsigned)(((long long)Vf * p.Ls + tpb - 1) / tpb), p.nrhs);
+  using vec = typename P::vec;
+  using tvec = typename P::tvec;
+  if (dag)
+    halo_pack_kernel<P, true><<<grid, tpb, 0, st>>>(
+        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gmain,
+        (const tvec *)p.gtail, p.V4, Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
+  else
+    halo_pack_kernel<P, false><<<grid, tpb, 0, st>>>(
+        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gmain,
+        (const tvec *)p.gtail, p.V4, Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <class P, int OP, int SPT, int VAR>
 __global__ void dslash_kernel(const DslashParams p) {
   using C = typename P::C;
@@ -617,14 +740,30 @@ __global__ void dslash_kernel(const DslashParams p) {
   constexpr int SB = -SF;           // sign S of the backward hop
 
   // CTAs are RHS-major (consecutive CTAs = the same sites for successive RHS),
-  // so the links of a tile are reused from L2 across right-hand sides.
+  // so the links of a tile are reused from L2 across right-hand sides.  Tiles
+  // are tx consecutive sites of one (x, y) plane; planes are visited z-block
+  // by z-block (zblk blocks of Lz / zblk planes), t inside a block, so a
+  // spinor's last use as a t-neighbour follows its first use by 2 Lz/zblk
+  // planes instead of 2 Lz: the L2 then holds the reuse window.
   const int tx = blockDim.x;
   const int rhs = blockIdx.x % p.nrhs;
-  const int x4 = (blockIdx.x / p.nrhs) * tx + threadIdx.x;
+  int x4, in_plane;
+  {
+    int id = blockIdx.x / p.nrhs;
+    const int tile = id % p.tiles_per_plane;
+    id /= p.tiles_per_plane;
+    const int bz = p.L[2] / p.zblk;
+    const int zl = id % bz;
+    id /= bz;
+    const int t = id % p.L[3];
+    const int zb = id / p.L[3];
+    in_plane = tile * tx + threadIdx.x;
+    x4 = in_plane + p.L[0] * p.L[1] * ((zb * bz + zl) + p.L[2] * t);
+  }
   const int chunk = threadIdx.y;
   const int nchunk = blockDim.y;
   if (p.gate && !p.gate[(long long)rhs * p.gate_stride]) return;  // whole CTA: uniform
-  const bool active = x4 < p.V4;
+  const bool active = in_plane < p.L[0] * p.L[1];
   const int s0 = chunk * SPT;
   const int Ls = p.Ls;
 
@@ -672,8 +811,20 @@ __global__ void dslash_kernel(const DslashParams p) {
 
   if (VAR == 0) {
     if (active) {
-      hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gmain, gtail, nb[0], x4, s0, Ls, b, c, mf);
-      hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[1], nb[1], s0, Ls, b, c, mf);
+      // t faces of a sub-lattice take their t-neighbours from the halos
+      const int Vf = p.L[0] * p.L[1] * p.L[2];
+      const int ct = x4 / Vf;
+      const long long hplane = (long long)Ls * Vf;
+      const long long hrhs = hplane * (12 / P::R);
+      if (p.halo_up && ct == p.L[3] - 1)
+        halo_hop_up<P, SF, true, SPT>(acc, (const vec *)p.halo_up + rhs * hrhs, hplane, Vf,
+                                      x4 - ct * Vf, gmain, gtail, x4, p.V4, s0);
+      else
+        hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gmain, gtail, nb[0], x4, s0, Ls, b, c, mf);
+      if (p.halo_dn && ct == 0)
+        halo_hop_down<P, SB, SPT>(acc, (const vec *)p.halo_dn + rhs * hrhs, hplane, Vf, x4, s0);
+      else
+        hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[1], nb[1], s0, Ls, b, c, mf);
       hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[2], x4, s0, Ls, b, c, mf);
       hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[3], nb[3], s0, Ls, b, c, mf);
       hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[4], x4, s0, Ls, b, c, mf);
@@ -793,10 +944,14 @@ size_t dslash_smem(int tx, int nchunk) {
 }
 
 template <class P, int OP, int SPT, int VAR>
-int launch_one(const DslashParams &p, int tx, cudaStream_t st) {
+int launch_one(const DslashParams &p, int tx, int zblk, cudaStream_t st) {
   const int nchunk = p.Ls / SPT;
   dim3 block(tx, nchunk);
-  dim3 grid((unsigned)(((long long)p.V4 + tx - 1) / tx * p.nrhs));
+  DslashParams q = p;
+  q.tiles_per_plane = (p.L[0] * p.L[1] + tx - 1) / tx;
+  q.zblk = zblk;
+  if (zblk < 1 || p.L[2] % zblk) return -2;
+  dim3 grid((unsigned)((long long)q.tiles_per_plane * p.L[2] * p.L[3] * p.nrhs));
   const size_t smem = dslash_smem<P, OP, SPT, VAR>(tx, nchunk);
   // per-instantiation launch limits, queried once
   static int max_threads = 0;
@@ -815,17 +970,17 @@ int launch_one(const DslashParams &p, int tx, cudaStream_t st) {
       return -3;
     smem_set = smem;
   }
-  dslash_kernel<P, OP, SPT, VAR><<<grid, block, smem, st>>>(p);
+  dslash_kernel<P, OP, SPT, VAR><<<grid, block, smem, st>>>(q);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <class P, int OP, int VAR>
 int launch_spt(const DslashParams &p, TileConfig cfg, cudaStream_t st) {
   switch (cfg.spt) {
-    case 1: return launch_one<P, OP, 1, VAR>(p, cfg.tx, st);
-    case 2: return launch_one<P, OP, 2, VAR>(p, cfg.tx, st);
-    case 3: return launch_one<P, OP, 3, VAR>(p, cfg.tx, st);
-    case 4: return launch_one<P, OP, 4, VAR>(p, cfg.tx, st);
+    case 1: return launch_one<P, OP, 1, VAR>(p, cfg.tx, cfg.zblk, st);
+    case 2: return launch_one<P, OP, 2, VAR>(p, cfg.tx, cfg.zblk, st);
+    case 3: return launch_one<P, OP, 3, VAR>(p, cfg.tx, cfg.zblk, st);
+    case 4: return launch_one<P, OP, 4, VAR>(p, cfg.tx, cfg.zblk, st);
     default: return -2;
   }
 }
@@ -901,5 +1056,14 @@ int max_threads_variant(int op, int spt) {
   }                                                                                      \
   int dslash_max_threads_##PREC##_v##VAR(int op, int spt) {                              \
     return max_threads_variant<PREC, VAR>(op, spt);                                      \
+  }                                                                                      \
+  }
+
+// Face packing for the t decomposition, one translation unit per precision.
+#define DW_HALO_INSTANTIATE(PREC)                                                         \
+  namespace dw {                                                                         \
+  int launch_halo_pack_##PREC(const DslashParams &p, void *send_dn, void *send_up, int dag, \
+                              cudaStream_t st) {                                         \
+    return launch_halo_pack_impl<PREC>(p, send_dn, send_up, dag, st);                    \
   }                                                                                      \
   }

@@ -1,0 +1,4 @@
+// F32 face packing for the t decomposition of the stencil ("virtual ranks").
+#include "dw_dslash.cuh"
+
+DW_HALO_INSTANTIATE(F32)

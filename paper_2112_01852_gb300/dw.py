@@ -52,7 +52,8 @@ SYMBOLS = (
     "dw_create_lattice", "dw_destroy_lattice", "dw_load_gauge", "dw_apply_Dhop",
     "dw_apply_Dhop_dag", "dw_apply_D", "dw_apply_Ddag", "dw_apply_DdagD",
     "dw_apply_DdagD_noalloc", "dw_apply_host",
-    "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_fermion_bytes", "dw_pack_fermion",
+    "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_halo_bytes", "dw_halo_pack",
+    "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
     "dw_unpack_fermion", "dw_last_error",
 )
 
@@ -103,8 +104,11 @@ def load_library():
             "dw_apply_DdagD_noalloc": (I, [P, P, P, DP, I, P]),
             "dw_apply_host": (I, [P, I, P, P, DP, I, P]),
             "dw_cg_solve": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
-            "dw_set_tile": (I, [P, I, I, I, I, I, I]),
-            "dw_tune": (I, [P, I, I, IP, IP, IP, P]),
+            "dw_set_tile": (I, [P, I, I, I, I, I, I, I]),
+            "dw_tune": (I, [P, I, I, IP, IP, IP, IP, P]),
+            "dw_halo_bytes": (S, [P, I, I]),
+            "dw_halo_pack": (I, [P, P, P, P, I, I, P]),
+            "dw_apply_Dhop_halo": (I, [P, P, P, P, P, I, I, P]),
             "dw_fermion_bytes": (S, [P, I, I]),
             "dw_pack_fermion": (I, [P, P, I, P, I, P]),
             "dw_unpack_fermion": (I, [P, P, P, I, I, P]),
@@ -197,19 +201,30 @@ def dw_cg_solve(lat, x, b, mf, nrhs, tol, maxit, mode, stream=0):
     return rc, list(stats)
 
 
-def dw_set_tile(lat, op, prec, nrhs, spt, tx, variant=0):
+def dw_set_tile(lat, op, prec, nrhs, spt, tx, variant=0, zblk=0):
     _check(load_library().dw_set_tile(lat, int(op), int(prec), int(nrhs), int(spt), int(tx),
-                                      int(variant)))
+                                      int(variant), int(zblk)))
 
 
 def dw_tune(lat, op, nrhs, stream=0):
-    """Returns the chosen (spt, tx, variant)."""
-    spt = ctypes.c_int()
-    tx = ctypes.c_int()
-    var = ctypes.c_int()
-    _check(load_library().dw_tune(lat, int(op), int(nrhs), ctypes.byref(spt), ctypes.byref(tx),
-                                  ctypes.byref(var), stream))
-    return spt.value, tx.value, var.value
+    """Returns the chosen (spt, tx, variant, zblk)."""
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(load_library().dw_tune(lat, int(op), int(nrhs), *[ctypes.byref(v) for v in vals],
+                                  stream))
+    return tuple(v.value for v in vals)
+
+
+def dw_halo_bytes(lat, prec, nrhs):
+    return int(load_library().dw_halo_bytes(lat, int(prec), int(nrhs)))
+
+
+def dw_halo_pack(lat, send_dn, send_up, inp, nrhs, dag=0, stream=0):
+    _check(load_library().dw_halo_pack(lat, send_dn, send_up, inp, int(nrhs), int(dag), stream))
+
+
+def dw_apply_Dhop_halo(lat, out, inp, recv_up, recv_dn, nrhs, dag=0, stream=0):
+    _check(load_library().dw_apply_Dhop_halo(lat, out, inp, recv_up, recv_dn, int(nrhs),
+                                             int(dag), stream))
 
 
 def dw_fermion_bytes(lat, prec, nrhs):

@@ -86,7 +86,7 @@ def test_all_tiles_ragged(Ls):
         for spt, tx in valid_tiles(Ls):
             for op in STENCIL_OPS:
                 try:
-                    lat.set_tile(op, spt, tx, variant)
+                    lat.set_tile(op, spt, tx, variant, zblk=1 + (spt + tx // 32) % 2)
                 except dw.DWError as e:  # variant not built at FP64, or CTA too large
                     assert e.code == dw.DW_ERR_ARG
                     continue
@@ -227,7 +227,8 @@ def test_tune_picks_valid_tile_and_stays_exact():
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
     lat.load_gauge(U)
     for op in STENCIL_OPS:
-        spt, tx, variant = lat.tune(op, 1)
+        spt, tx, variant, zblk = lat.tune(op, 1)
+        assert dims[2] % zblk == 0
         assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
         assert variant in range(4)
         got = run_gpu(lat, op, psi, mf=[0.01])
@@ -276,6 +277,9 @@ def test_argument_errors():
     assert e.value.code == dw.DW_ERR_ARG
     with pytest.raises(dw.DWError) as e:
         lat.set_tile(dw.DW_OP_DHOP, 1, 32, variant=5)
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        lat.set_tile(dw.DW_OP_DHOP, 1, 32, zblk=3)  # 3 does not divide Lz = 4
     assert e.value.code == dw.DW_ERR_ARG
     assert "multiple" in dw.dw_last_error() or "invalid" in dw.dw_last_error()
     torch.cuda.synchronize()
