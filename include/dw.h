@@ -32,12 +32,17 @@
  *    message.  A failed argument check launches nothing.
  *  - `out` must not alias `in`.
  *
- * Internal fermion layout (per RHS): planes [p][s][x4] of 16-byte vectors
- * (8-byte for DW_F16), x4 = x + Lx*(y + Ly*(z + Lz*t)).  The 24 reals of a 5D
- * site are ordered I = half*12 + c*4 + ri*2 + j (chirality half: 0 = spins 0,1
- * (P+), 1 = spins 2,3 (P-); colour c; re/im ri; spin j within the half), so
- * each run of 4 reals is the spin pair (Re, Re, Im, Im) of one colour; plane p
- * holds reals [p*R, p*R + R) with R = 2 (F64) or 4 (F32, F16).
+ * Internal fermion layout (per RHS): sites are grouped in blocks of 32
+ * consecutive x4 = x + Lx*(y + Ly*(z + Lz*t)); plane p of site (x4, s) is the
+ * 16-byte vector (8-byte for DW_F16) at index
+ *   ((x4 / 32) * Ls + s) * NP * 32 + p * 32 + x4 % 32,   NP = 24 / R,
+ * so every block keeps all its slices and planes contiguous.  V4 is padded to
+ * a multiple of 32 (dw_fermion_bytes includes the padding; padding lanes are
+ * ignored).  The 24 reals of a 5D site are ordered I = half*12 + c*4 + ri*2 + j
+ * (chirality half: 0 = spins 0,1 (P+), 1 = spins 2,3 (P-); colour c; re/im ri;
+ * spin j within the half), so each run of 4 reals is the spin pair
+ * (Re, Re, Im, Im) of one colour; plane p holds reals [p*R, p*R + R) with
+ * R = 2 (F64) or 4 (F32, F16).
  *
  * Canonical layout (dw_pack_fermion / dw_unpack_fermion / dw_load_gauge):
  *   fermion complex128 [rhs][x4][s][spin 4][colour 3]

@@ -33,7 +33,8 @@ int cuda_fail(cudaError_t e, const char *what) {
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 size_t field_bytes(const dw_lattice *lat, int prec, int nrhs) {
-  return (size_t)24 * (size_t)lat->V5 * (size_t)prec_real_bytes(prec) * (size_t)nrhs;
+  return (size_t)24 * (size_t)lat->V4p * (size_t)lat->Ls * (size_t)prec_real_bytes(prec) *
+         (size_t)nrhs;
 }
 
 FieldGeom geom(const dw_lattice *lat) {
@@ -134,8 +135,8 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
     p.V4 = (int)lat->V4;
     p.Ls = lat->Ls;
-    p.plane = lat->V5;
-    p.rhs_stride = lat->V5 * (24 / prec_reals_per_vec(prec));
+    p.plane = kPlaneStride;
+    p.rhs_stride = lat->V4p * lat->Ls * (24 / prec_reals_per_vec(prec));
     p.nrhs = n;
     p.gate = gate ? gate + (size_t)r0 * gate_stride : nullptr;
     p.gate_stride = gate_stride;
@@ -233,6 +234,7 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
   lat->Ls = Ls;
   lat->V4 = V4;
   lat->V5 = V4 * Ls;
+  lat->V4p = padded_v4(V4);
   lat->kind = kind;
   lat->M5 = M5;
   lat->b = kind == DW_SHAMIR ? 1.0 : b;
@@ -410,8 +412,8 @@ int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, 
   for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
   p.V4 = (int)lat->V4;
   p.Ls = lat->Ls;
-  p.plane = lat->V5;
-  p.rhs_stride = lat->V5 * (24 / prec_reals_per_vec(lat->prec));
+  p.plane = kPlaneStride;
+  p.rhs_stride = lat->V4p * lat->Ls * (24 / prec_reals_per_vec(lat->prec));
   p.nrhs = nrhs;
   int rc;
   switch (lat->prec) {

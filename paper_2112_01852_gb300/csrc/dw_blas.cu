@@ -11,33 +11,46 @@
 
 namespace dw {
 
+// Quad q (4 reals) of site slot j of the blocked layout: slot j covers the
+// 32-lane block j/32 (all slices in turn) and lane j%32.
 template <class P, class A>
-__device__ __forceinline__ void ld4(A *r, const void *base, int q, long long i, long long plane) {
-  const typename P::vec *b = (const typename P::vec *)base;
+__device__ __forceinline__ void ld4(A *r, const void *base, int q, long long j) {
+  const typename P::vec *b =
+      (const typename P::vec *)base + (j >> 5) * (24 / P::R) * 32 + (j & 31);
   typename P::C t[4];
   if (P::R == 4) {
-    load_vec<P>(t, b + q * plane + i);
+    load_vec<P>(t, b + q * 32);
   } else {
-    load_vec<P>(t, b + 2 * q * plane + i);
-    load_vec<P>(t + 2, b + (2 * q + 1) * plane + i);
+    load_vec<P>(t, b + 2 * q * 32);
+    load_vec<P>(t + 2, b + (2 * q + 1) * 32);
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = (A)t[k];
 }
 
 template <class P, class A>
-__device__ __forceinline__ void st4(void *base, int q, long long i, long long plane, const A *r) {
-  typename P::vec *b = (typename P::vec *)base;
+__device__ __forceinline__ void st4(void *base, int q, long long j, const A *r) {
+  typename P::vec *b = (typename P::vec *)base + (j >> 5) * (24 / P::R) * 32 + (j & 31);
   typename P::C t[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) t[k] = (typename P::C)r[k];
   if (P::R == 4) {
-    store_vec<P>(b + q * plane + i, t);
+    store_vec<P>(b + q * 32, t);
   } else {
-    store_vec<P>(b + 2 * q * plane + i, t);
-    store_vec<P>(b + (2 * q + 1) * plane + i, t + 2);
+    store_vec<P>(b + 2 * q * 32, t);
+    store_vec<P>(b + (2 * q + 1) * 32, t + 2);
   }
 }
+
+// Slot j holds a lattice site (not a padding lane of the last block).
+__device__ __forceinline__ bool real_slot(long long j, int V4, int Ls) {
+  return (int)((j >> 5) / Ls) * 32 + (int)(j & 31) < V4;
+}
+
+#define SLOT_LOOP(j)                                                                     \
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < L.nslot;     \
+       j += (long long)gridDim.x * blockDim.x)                                           \
+    if (real_slot(j, L.V4, L.Ls))
 
 // Arithmetic type of a kernel touching fields of precisions PA and PB: FP64
 // only when one of them is stored in FP64 (GB300's FP64 rate is far below its
@@ -68,7 +81,7 @@ __device__ __forceinline__ double block_sum(double v) {
 // partial[rhs][blockIdx.x] = sum over this block's sites of Re<a, b>
 template <class PA, class PB>
 __global__ void __launch_bounds__(kBlasThreads)
-    redot_kernel(const void *a, const void *b, long long V5, size_t ba, size_t bb,
+    redot_kernel(const void *a, const void *b, SlotGeom L, size_t ba, size_t bb,
                  double *partial, const CGState *st) {
   const int rhs = blockIdx.y;
   double s = 0.0;
@@ -76,14 +89,13 @@ __global__ void __launch_bounds__(kBlasThreads)
     const void *pa = RHS_PTR(const char *, a, rhs, ba);
     const void *pb = RHS_PTR(const char *, b, rhs, bb);
     using A = typename Arith<PA, PB>::T;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V5;
-         i += (long long)gridDim.x * blockDim.x) {
+    SLOT_LOOP(i) {
       A site = 0;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
         A x[4], y[4];
-        ld4<PA>(x, pa, q, i, V5);
-        ld4<PB>(y, pb, q, i, V5);
+        ld4<PA>(x, pa, q, i);
+        ld4<PB>(y, pb, q, i);
 #pragma unroll
         for (int k = 0; k < 4; ++k) site += x[k] * y[k];
       }
@@ -112,7 +124,7 @@ __global__ void finalize_sum_kernel(const double *partial, int nblk, double *out
 
 // r = b - Ax in FP64; partial |r|^2.  (All three F64 fields.)
 __global__ void __launch_bounds__(kBlasThreads)
-    residual_kernel(double *r, const double *b, const double *Ax, long long V5, size_t bytes,
+    residual_kernel(double *r, const double *b, const double *Ax, SlotGeom L, size_t bytes,
                     double *partial, const CGState *st) {
   const int rhs = blockIdx.y;
   double s = 0.0;
@@ -120,12 +132,19 @@ __global__ void __launch_bounds__(kBlasThreads)
     double *pr = RHS_PTR(double *, r, rhs, bytes);
     const double *pb = RHS_PTR(const double *, b, rhs, bytes);
     const double *pa = RHS_PTR(const double *, Ax, rhs, bytes);
-    const long long n = 24 * V5;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-      const double v = pb[i] - pa[i];
-      pr[i] = v;
-      s += v * v;
+    SLOT_LOOP(i) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        double bv[4], av[4];
+        ld4<F64>(bv, pb, q, i);
+        ld4<F64>(av, pa, q, i);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          bv[k] -= av[k];
+          s += bv[k] * bv[k];
+        }
+        st4<F64>(pr, q, i, bv);
+      }
     }
   }
   s = block_sum(s);
@@ -137,7 +156,7 @@ __global__ void __launch_bounds__(kBlasThreads)
 // state; run after the true residual has been reduced.
 template <class PP, class PR>
 __global__ void __launch_bounds__(kBlasThreads)
-    reliable_apply_kernel(const double *r, void *r_s, void *x_s, void *p, long long V5,
+    reliable_apply_kernel(const double *r, void *r_s, void *x_s, void *p, SlotGeom L,
                           size_t b64, size_t bpp, size_t bpr, const CGState *st) {
   const int rhs = blockIdx.y;
   const CGState &S = st[rhs];
@@ -148,21 +167,20 @@ __global__ void __launch_bounds__(kBlasThreads)
   void *prs = RHS_PTR(char *, r_s, rhs, bpr);
   void *pxs = RHS_PTR(char *, x_s, rhs, bpr);
   void *pp = RHS_PTR(char *, p, rhs, bpp);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V5;
-       i += (long long)gridDim.x * blockDim.x) {
+  SLOT_LOOP(i) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       double rv[4], pv[4], z[4] = {0.0, 0.0, 0.0, 0.0};
-      ld4<F64>(rv, pr, q, i, V5);
-      ld4<PP>(pv, pp, q, i, V5);
+      ld4<F64>(rv, pr, q, i);
+      ld4<PP>(pv, pp, q, i);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         rv[k] *= inv;
         pv[k] = rv[k] + bp * pv[k];
       }
-      st4<PR>(prs, q, i, V5, rv);
-      st4<PR>(pxs, q, i, V5, z);
-      st4<PP>(pp, q, i, V5, pv);
+      st4<PR>(prs, q, i, rv);
+      st4<PR>(pxs, q, i, z);
+      st4<PP>(pp, q, i, pv);
     }
   }
 }
@@ -170,7 +188,7 @@ __global__ void __launch_bounds__(kBlasThreads)
 // x (F64) += scale * x_s for RHS flagged need_update (scale = the old sigma).
 template <class PR>
 __global__ void __launch_bounds__(kBlasThreads)
-    accumulate_x_kernel(void *x, const void *x_s, long long V5, size_t b64, size_t bpr,
+    accumulate_x_kernel(void *x, const void *x_s, SlotGeom L, size_t b64, size_t bpr,
                         const CGState *st) {
   const int rhs = blockIdx.y;
   const CGState &S = st[rhs];
@@ -178,16 +196,15 @@ __global__ void __launch_bounds__(kBlasThreads)
   const double a = S.sigma;
   void *px = RHS_PTR(char *, x, rhs, b64);
   const void *pxs = RHS_PTR(const char *, x_s, rhs, bpr);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V5;
-       i += (long long)gridDim.x * blockDim.x) {
+  SLOT_LOOP(i) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       double xv[4], sv[4];
-      ld4<F64>(xv, px, q, i, V5);
-      ld4<PR>(sv, pxs, q, i, V5);
+      ld4<F64>(xv, px, q, i);
+      ld4<PR>(sv, pxs, q, i);
 #pragma unroll
       for (int k = 0; k < 4; ++k) xv[k] += a * sv[k];
-      st4<F64>(px, q, i, V5, xv);
+      st4<F64>(px, q, i, xv);
     }
   }
 }
@@ -195,7 +212,7 @@ __global__ void __launch_bounds__(kBlasThreads)
 // CG step: x_s += alpha p;  r_s -= alpha Ap;  partial |r_s|^2  (active RHS only)
 template <class PP, class PR>
 __global__ void __launch_bounds__(kBlasThreads)
-    cg_update_kernel(void *x_s, void *r_s, const void *p, const void *Ap, long long V5,
+    cg_update_kernel(void *x_s, void *r_s, const void *p, const void *Ap, SlotGeom L,
                      size_t bpp, size_t bpr, double *partial, const CGState *st) {
   const int rhs = blockIdx.y;
   const CGState &S = st[rhs];
@@ -208,24 +225,23 @@ __global__ void __launch_bounds__(kBlasThreads)
     const void *pap = RHS_PTR(const char *, Ap, rhs, bpp);
     using A = typename Arith<PP, PR>::T;
     const A a = (A)alpha;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V5;
-         i += (long long)gridDim.x * blockDim.x) {
+    SLOT_LOOP(i) {
       A site = 0;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
         A xv[4], rv[4], pv[4], av[4];
-        ld4<PR>(xv, pxs, q, i, V5);
-        ld4<PR>(rv, prs, q, i, V5);
-        ld4<PP>(pv, pp, q, i, V5);
-        ld4<PP>(av, pap, q, i, V5);
+        ld4<PR>(xv, pxs, q, i);
+        ld4<PR>(rv, prs, q, i);
+        ld4<PP>(pv, pp, q, i);
+        ld4<PP>(av, pap, q, i);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           xv[k] += a * pv[k];
           rv[k] -= a * av[k];
           site += rv[k] * rv[k];
         }
-        st4<PR>(pxs, q, i, V5, xv);
-        st4<PR>(prs, q, i, V5, rv);
+        st4<PR>(pxs, q, i, xv);
+        st4<PR>(prs, q, i, rv);
       }
       s += (double)site;
     }
@@ -237,7 +253,7 @@ __global__ void __launch_bounds__(kBlasThreads)
 // p = r_s + beta p  (active RHS that continue without a reliable update)
 template <class PP, class PR>
 __global__ void __launch_bounds__(kBlasThreads)
-    cg_direction_kernel(void *p, const void *r_s, long long V5, size_t bpp, size_t bpr,
+    cg_direction_kernel(void *p, const void *r_s, SlotGeom L, size_t bpp, size_t bpr,
                         const CGState *st) {
   const int rhs = blockIdx.y;
   const CGState &S = st[rhs];
@@ -246,16 +262,15 @@ __global__ void __launch_bounds__(kBlasThreads)
   const A b = (A)S.beta;
   void *pp = RHS_PTR(char *, p, rhs, bpp);
   const void *prs = RHS_PTR(const char *, r_s, rhs, bpr);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V5;
-       i += (long long)gridDim.x * blockDim.x) {
+  SLOT_LOOP(i) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       A pv[4], rv[4];
-      ld4<PP>(pv, pp, q, i, V5);
-      ld4<PR>(rv, prs, q, i, V5);
+      ld4<PP>(pv, pp, q, i);
+      ld4<PR>(rv, prs, q, i);
 #pragma unroll
       for (int k = 0; k < 4; ++k) pv[k] = rv[k] + b * pv[k];
-      st4<PP>(pp, q, i, V5, pv);
+      st4<PP>(pp, q, i, pv);
     }
   }
 }
@@ -387,14 +402,18 @@ __global__ void cg_clear_update_kernel(CGState *st, int nrhs) {
 // ---------------------------------------------------------------------------
 // Host launchers
 
-static unsigned grid_for(long long V5, int num_sms) {
-  long long want = (V5 + kBlasThreads - 1) / kBlasThreads;
+static unsigned grid_for(long long nslot, int num_sms) {
+  long long want = (nslot + kBlasThreads - 1) / kBlasThreads;
   long long cap = (long long)num_sms * 4;
   return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-BlasCtx::BlasCtx(long long V5_, int nrhs_, int num_sms_) : V5(V5_), nrhs(nrhs_) {
-  nblk = (int)grid_for(V5_, num_sms_);
+BlasCtx::BlasCtx(int V4, int Ls, int nrhs_, int num_sms_) : nrhs(nrhs_) {
+  geom.V4 = V4;
+  geom.Ls = Ls;
+  geom.nslot = padded_v4(V4) * Ls;
+  nreal = 24.0 * (double)V4 * Ls;
+  nblk = (int)grid_for(geom.nslot, num_sms_);
 }
 
 #define DISPATCH_PREC(prec, T, ...)            \
@@ -405,16 +424,16 @@ BlasCtx::BlasCtx(long long V5_, int nrhs_, int num_sms_) : V5(V5_), nrhs(nrhs_) 
     default: return -2;                        \
   }
 
-static size_t rbytes(int prec, long long V5) {
-  return (size_t)24 * V5 * (prec == DW_F64 ? 8 : prec == DW_F32 ? 4 : 2);
+static size_t rbytes(int prec, const SlotGeom &g) {
+  return (size_t)24 * g.nslot * (prec == DW_F64 ? 8 : prec == DW_F32 ? 4 : 2);
 }
 
 int blas_redot(const BlasCtx &c, int pa, const void *a, int pb, const void *b, double *partial,
                const CGState *st, cudaStream_t s) {
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pa, PA, DISPATCH_PREC(pb, PB,
-      redot_kernel<PA, PB><<<grid, kBlasThreads, 0, s>>>(a, b, c.V5, rbytes(pa, c.V5),
-                                                         rbytes(pb, c.V5), partial, st)));
+      redot_kernel<PA, PB><<<grid, kBlasThreads, 0, s>>>(a, b, c.geom, rbytes(pa, c.geom),
+                                                         rbytes(pb, c.geom), partial, st)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -426,8 +445,8 @@ int blas_finalize_sum(const BlasCtx &c, const double *partial, double *out, cuda
 int cg_residual(const BlasCtx &c, double *r, const double *b, const double *Ax, double *partial,
                 const CGState *st, cudaStream_t s) {
   dim3 grid(c.nblk, c.nrhs);
-  residual_kernel<<<grid, kBlasThreads, 0, s>>>(r, b, Ax, c.V5, rbytes(DW_F64, c.V5), partial,
-                                                st);
+  residual_kernel<<<grid, kBlasThreads, 0, s>>>(r, b, Ax, c.geom, rbytes(DW_F64, c.geom),
+                                                partial, st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -435,8 +454,8 @@ int cg_accumulate_x(const BlasCtx &c, int pr, void *x, const void *x_s, const CG
                     cudaStream_t s) {
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pr, PR,
-      accumulate_x_kernel<PR><<<grid, kBlasThreads, 0, s>>>(x, x_s, c.V5, rbytes(DW_F64, c.V5),
-                                                            rbytes(pr, c.V5), st));
+      accumulate_x_kernel<PR><<<grid, kBlasThreads, 0, s>>>(
+          x, x_s, c.geom, rbytes(DW_F64, c.geom), rbytes(pr, c.geom), st));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -445,7 +464,8 @@ int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pp, PP, DISPATCH_PREC(pr, PR,
       reliable_apply_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
-          r, r_s, x_s, p, c.V5, rbytes(DW_F64, c.V5), rbytes(pp, c.V5), rbytes(pr, c.V5), st)));
+          r, r_s, x_s, p, c.geom, rbytes(DW_F64, c.geom), rbytes(pp, c.geom), rbytes(pr, c.geom),
+          st)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -454,7 +474,7 @@ int cg_update(const BlasCtx &c, int pp, int pr, void *x_s, void *r_s, const void
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pp, PP, DISPATCH_PREC(pr, PR,
       cg_update_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
-          x_s, r_s, p, Ap, c.V5, rbytes(pp, c.V5), rbytes(pr, c.V5), partial, st)));
+          x_s, r_s, p, Ap, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), partial, st)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -463,7 +483,7 @@ int cg_direction(const BlasCtx &c, int pp, int pr, void *p, const void *r_s, con
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pp, PP, DISPATCH_PREC(pr, PR,
       cg_direction_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
-          p, r_s, c.V5, rbytes(pp, c.V5), rbytes(pr, c.V5), st)));
+          p, r_s, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), st)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -481,12 +501,12 @@ int cg_beta(const BlasCtx &c, const double *partial, CGState *st, double delta, 
 int cg_reliable(const BlasCtx &c, const double *partial, CGState *st, double tol, int maxit,
                 int first, cudaStream_t s) {
   cg_reliable_kernel<<<c.nrhs, 32, 0, s>>>(partial, c.nblk, st, tol, maxit, first,
-                                           24.0 * (double)c.V5);
+                                           c.nreal);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int cg_install(const BlasCtx &c, CGState *st, cudaStream_t s) {
-  cg_install_kernel<<<(c.nrhs + 63) / 64, 64, 0, s>>>(st, c.nrhs, 24.0 * (double)c.V5);
+  cg_install_kernel<<<(c.nrhs + 63) / 64, 64, 0, s>>>(st, c.nrhs, c.nreal);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

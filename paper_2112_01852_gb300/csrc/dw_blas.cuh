@@ -33,11 +33,19 @@ struct CGState {
 
 constexpr int kCGStateInts = sizeof(CGState) / sizeof(int);
 
+// Site slots of the blocked layout: nslot = padded V4 * Ls.
+struct SlotGeom {
+  long long nslot;
+  int V4;
+  int Ls;
+};
+
 struct BlasCtx {
-  long long V5;
+  SlotGeom geom;
+  double nreal;  // reals per RHS on real sites (24 V4 Ls)
   int nrhs;
   int nblk;  // blocks per RHS of the reduction kernels
-  BlasCtx(long long V5_, int nrhs_, int num_sms);
+  BlasCtx(int V4, int Ls, int nrhs_, int num_sms);
 };
 
 int blas_redot(const BlasCtx &c, int pa, const void *a, int pb, const void *b, double *partial,

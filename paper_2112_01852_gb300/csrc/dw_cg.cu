@@ -147,7 +147,7 @@ extern "C" int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double
   if (e != cudaSuccess) return cuda_fail(e, "caller stream synchronize");
 
   Solve S{lat, w, nrhs, mode, mode == DW_F64 ? DW_F64 : DW_F32, mode == DW_F64 ? 0.0 : 0.1,
-          tol, maxit, mf, w->stream, BlasCtx(lat->V5, nrhs, lat->num_sms)};
+          tol, maxit, mf, w->stream, BlasCtx((int)lat->V4, lat->Ls, nrhs, lat->num_sms)};
   const size_t f64 = field_bytes(lat, DW_F64, nrhs);
   const size_t fpp = field_bytes(lat, S.pp, nrhs);
   const size_t fpr = field_bytes(lat, S.pr, nrhs);

@@ -145,6 +145,20 @@ __device__ __forceinline__ void store_vec(typename P::vec *p, const typename P::
 }
 
 // ---------------------------------------------------------------------------
+// Blocked fermion layout.  Sites are grouped in blocks of 32 consecutive x4
+// (the lanes of a warp); within a field of npv vec planes per site, plane p of
+// site (x4, s) is at vec offset ((x4/32)*Ls + s)*npv*32 + p*32 + x4%32.  All
+// slices and planes of one block are contiguous (npv*32*Ls vecs), so the data
+// a CTA touches for one row of sites is one contiguous run of memory.  V4 is
+// padded to a multiple of 32; the padding lanes are never read as neighbours,
+// never written, and skipped by the reductions.
+constexpr int kPlaneStride = 32;  // vecs between consecutive planes of one site
+__host__ __device__ __forceinline__ long long site_off(int x4, int s, int Ls, int npv) {
+  return ((long long)(x4 >> 5) * Ls + s) * npv * 32 + (x4 & 31);
+}
+__host__ __device__ __forceinline__ long long padded_v4(long long V4) { return (V4 + 31) / 32 * 32; }
+
+// ---------------------------------------------------------------------------
 // Operator kinds handled by the stencil kernel.
 enum OpKind { OP_DHOP = 0, OP_DHOP_DAG = 1, OP_D = 2, OP_DDAG = 3 };
 
@@ -156,8 +170,8 @@ struct DslashParams {
   int L[4];
   int V4;
   int Ls;
-  long long plane;       // vecs per fermion plane (= Ls * V4)
-  long long rhs_stride;  // vecs per right-hand side (= 24/R planes)
+  long long plane;       // vecs between consecutive planes of one site (kPlaneStride)
+  long long rhs_stride;  // vecs per right-hand side (= padded V4 * Ls * 24/R)
   int nrhs;             // right-hand sides in this launch (<= kMaxRhsPerLaunch)
   const int *gate;      // optional: CTAs of RHS r run only if gate[r * gate_stride] != 0
   int gate_stride;
@@ -204,6 +218,7 @@ struct dw_lattice {
   int dims[4];
   int Ls;
   long long V4;
+  long long V4p;  // V4 padded to a multiple of 32 (blocked layout)
   long long V5;
   int kind;
   double M5, b, c;

@@ -223,12 +223,15 @@ struct Field {
   using vec = typename P::vec;
   using V2 = typename Pair<P>::type;
   static constexpr int VPQ = 4 / P::R;  // vecs (planes) per quad
+  static constexpr int NPV = 24 / P::R;  // vec planes per site
+  static constexpr long long plane = kPlaneStride;
   const vec *base;
-  long long plane;
   int V4;
+  int Ls;
+  __device__ __forceinline__ long long site(int s, int x4) const { return site_off(x4, s, Ls, NPV); }
   // half = 0: upper spins, 1: lower spins, at (x4, s)
   __device__ __forceinline__ void load_half(Half<V2> &h, int x4, int s, int half) const {
-    const vec *p = base + (long long)half * 3 * VPQ * plane + (long long)s * V4 + x4;
+    const vec *p = base + site(s, x4) + (long long)half * 3 * VPQ * plane;
 #pragma unroll
     for (int c = 0; c < 3; ++c) quad_in(h.re[c], h.im[c], p + (long long)c * VPQ * plane, plane);
   }
@@ -419,7 +422,7 @@ struct StagedHop {
     if (!PHI) {
 #pragma unroll
       for (int j = 0; j < SPT; ++j) {
-        const vec *sp = F.base + (long long)(s0 + j) * F.V4 + y4;
+        const vec *sp = F.base + F.site(s0 + j, y4);
 #pragma unroll
         for (int k = 0; k < 6 * VPQ; ++k)
           cp_async<sizeof(vec)>(vslot(stage, j * 6 * VPQ + k), sp + (long long)k * F.plane);
@@ -431,8 +434,8 @@ struct StagedHop {
         if (su < 0) su = Ls - 1;
         int sl = s0 + i;
         if (sl == Ls) sl = 0;
-        const vec *pu = F.base + (long long)su * F.V4 + y4;
-        const vec *pl = F.base + (long long)sl * F.V4 + y4 + (long long)3 * VPQ * F.plane;
+        const vec *pu = F.base + F.site(su, y4);
+        const vec *pl = F.base + F.site(sl, y4) + (long long)3 * VPQ * F.plane;
 #pragma unroll
         for (int k = 0; k < 3 * VPQ; ++k) {
           cp_async<sizeof(vec)>(vslot(stage, i * 3 * VPQ + k), pu + (long long)k * F.plane);
@@ -679,8 +682,9 @@ __global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send
   const int s = (int)(i / Vf);
   Field<P> F;
   F.base = in + (long long)rhs * rhs_stride;
-  F.plane = plane;
   F.V4 = V4;
+  F.Ls = Ls;
+  (void)plane;
   {  // first slice -> rank below
     Spinor<V2> v;
     F.load_half(v.up, face, s, 0);
@@ -769,8 +773,8 @@ __global__ void dslash_kernel(const DslashParams p) {
 
   Field<P> F;
   F.base = reinterpret_cast<const vec *>(p.in) + (long long)rhs * p.rhs_stride;
-  F.plane = p.plane;
   F.V4 = p.V4;
+  F.Ls = p.Ls;
   vec *out = reinterpret_cast<vec *>(p.out) + (long long)rhs * p.rhs_stride;
   const vec *gmain = reinterpret_cast<const vec *>(p.gmain);
   const tvec *gtail = reinterpret_cast<const tvec *>(p.gtail);
@@ -857,7 +861,7 @@ __global__ void dslash_kernel(const DslashParams p) {
   }
 
   auto store = [&](int j, const Spinor<V2> &v) {
-    store_spinor<P>(out + (long long)(s0 + j) * p.V4 + x4, p.plane, v);
+    store_spinor<P>(out + F.site(s0 + j, x4), kPlaneStride, v);
   };
   const V2 mhalf = bc<V2>(C(-0.5));
 

@@ -17,40 +17,40 @@ __device__ __forceinline__ int canon_real(int I) {
 }
 template <class P>
 __global__ void pack_kernel(typename P::vec *dst, const double *src, long long V5, int V4,
-                            int Ls, long long plane, long long rhs_stride) {
+                            int Ls, long long rhs_stride) {
+  constexpr int NP = 24 / P::R;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y;
   if (i >= V5) return;
   const int x4 = (int)(i / Ls);
   const int s = (int)(i % Ls);
   const double *p = src + ((long long)rhs * V5 + i) * 24;
-  typename P::vec *d = dst + (long long)rhs * rhs_stride + (long long)s * V4 + x4;
-  constexpr int NP = 24 / P::R;
+  typename P::vec *d = dst + (long long)rhs * rhs_stride + site_off(x4, s, Ls, NP);
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     double r[P::R];
 #pragma unroll
     for (int k = 0; k < P::R; ++k) r[k] = p[canon_real(q * P::R + k)];
-    d[q * plane] = narrow_from_f64(r, (typename P::vec *)nullptr);
+    d[q * kPlaneStride] = narrow_from_f64(r, (typename P::vec *)nullptr);
   }
 }
 
 template <class P>
 __global__ void unpack_kernel(double *dst, const typename P::vec *src, long long V5, int V4,
-                              int Ls, long long plane, long long rhs_stride) {
+                              int Ls, long long rhs_stride) {
   using C = typename P::C;
+  constexpr int NP = 24 / P::R;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y;
   if (i >= V5) return;
   const int x4 = (int)(i / Ls);
   const int s = (int)(i % Ls);
   double *p = dst + ((long long)rhs * V5 + i) * 24;
-  const typename P::vec *sp = src + (long long)rhs * rhs_stride + (long long)s * V4 + x4;
-  constexpr int NP = 24 / P::R;
+  const typename P::vec *sp = src + (long long)rhs * rhs_stride + site_off(x4, s, Ls, NP);
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     C r[P::R];
-    load_vec<P>(r, sp + q * plane);
+    load_vec<P>(r, sp + q * kPlaneStride);
 #pragma unroll
     for (int k = 0; k < P::R; ++k) p[canon_real(q * P::R + k)] = (double)r[k];
   }
@@ -61,9 +61,8 @@ static int pack_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cuda
   const long long V5 = g.V5();
   const int tpb = 256;
   dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
-  const long long plane = (long long)g.Ls * g.V4;
   pack_kernel<P><<<grid, tpb, 0, st>>>((typename P::vec *)dst, (const double *)src, V5, g.V4,
-                                       g.Ls, plane, plane * (24 / P::R));
+                                       g.Ls, padded_v4(g.V4) * g.Ls * (24 / P::R));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -72,9 +71,8 @@ static int unpack_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cu
   const long long V5 = g.V5();
   const int tpb = 256;
   dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
-  const long long plane = (long long)g.Ls * g.V4;
   unpack_kernel<P><<<grid, tpb, 0, st>>>((double *)dst, (const typename P::vec *)src, V5, g.V4,
-                                         g.Ls, plane, plane * (24 / P::R));
+                                         g.Ls, padded_v4(g.V4) * g.Ls * (24 / P::R));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -153,57 +151,49 @@ int load_gauge(const FieldGeom &g, const int bc[4], const void *U, void *const g
 }
 
 // ---------------------------------------------------------------------------
-// Precision conversion between internal fields: one thread per "quad" (4
-// reals at one 5D site: plane q of F32/F16, planes 2q and 2q+1 of F64).
-template <class P>
-__device__ __forceinline__ void load_quad(typename P::C *r, const void *base, long long q,
-                                          long long i, long long plane) {
-  const typename P::vec *b = (const typename P::vec *)base;
-  if (P::R == 4) {
-    load_vec<P>(r, b + q * plane + i);
-  } else {
-    load_vec<P>(r, b + 2 * q * plane + i);
-    load_vec<P>(r + 2, b + (2 * q + 1) * plane + i);
-  }
-}
-
-template <class P>
-__device__ __forceinline__ void store_quad(void *base, long long q, long long i, long long plane,
-                                           const typename P::C *r) {
-  typename P::vec *b = (typename P::vec *)base;
-  if (P::R == 4) {
-    store_vec<P>(b + q * plane + i, r);
-  } else {
-    store_vec<P>(b + 2 * q * plane + i, r);
-    store_vec<P>(b + (2 * q + 1) * plane + i, r + 2);
-  }
-}
-
+// Precision conversion between internal fields: one thread per site slot of
+// the blocked layout (padding lanes skipped), all 6 quads (a quad is 4 reals:
+// plane q of F32/F16, planes 2q and 2q+1 of F64).
 template <class PI, class PO>
-__global__ void convert_kernel(void *dst, const void *src, long long V5, long long rhs_in,
-                               long long rhs_out) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void convert_kernel(void *dst, const void *src, long long nslot, int V4, int Ls,
+                               long long rhs_in, long long rhs_out) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y;
-  if (i >= V5) return;
-  const char *s = (const char *)src + rhs * rhs_in;
-  char *d = (char *)dst + rhs * rhs_out;
+  if (j >= nslot) return;
+  const int x4 = (int)((j >> 5) / Ls) * 32 + (int)(j & 31);
+  if (x4 >= V4) return;
+  const typename PI::vec *s =
+      (const typename PI::vec *)((const char *)src + rhs * rhs_in) + (j >> 5) * (24 / PI::R) * 32 + (j & 31);
+  typename PO::vec *d =
+      (typename PO::vec *)((char *)dst + rhs * rhs_out) + (j >> 5) * (24 / PO::R) * 32 + (j & 31);
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     typename PI::C a[4];
-    load_quad<PI>(a, s, q, i, V5);
     typename PO::C b[4];
+    if (PI::R == 4) {
+      load_vec<PI>(a, s + q * 32);
+    } else {
+      load_vec<PI>(a, s + 2 * q * 32);
+      load_vec<PI>(a + 2, s + (2 * q + 1) * 32);
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) b[k] = (typename PO::C)a[k];
-    store_quad<PO>(d, q, i, V5, b);
+    if (PO::R == 4) {
+      store_vec<PO>(d + q * 32, b);
+    } else {
+      store_vec<PO>(d + 2 * q * 32, b);
+      store_vec<PO>(d + (2 * q + 1) * 32, b + 2);
+    }
   }
 }
 
 template <class PI, class PO>
 static int convert_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cudaStream_t st) {
-  const long long V5 = g.V5();
+  const long long nslot = padded_v4(g.V4) * g.Ls;
   const int tpb = 256;
-  dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
-  convert_kernel<PI, PO><<<grid, tpb, 0, st>>>(dst, src, V5, 24 * V5 * PI::RB, 24 * V5 * PO::RB);
+  dim3 grid((unsigned)((nslot + tpb - 1) / tpb), nrhs);
+  convert_kernel<PI, PO><<<grid, tpb, 0, st>>>(dst, src, nslot, g.V4, g.Ls, 24 * nslot * PI::RB,
+                                               24 * nslot * PO::RB);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
