@@ -94,7 +94,9 @@ void dw_destroy_lattice(dw_lattice *lat);
 /*
  * Copy and convert a gauge field (DEVICE pointer, canonical complex128) into
  * the lattice's internal link arrays at every precision, folding the boundary
- * signs into the links that cross the lattice edge.  The caller may free U as
+ * signs into the links that cross the lattice edge.  The links must be SU(3)
+ * (unitary, determinant 1): the FP32 and FP16 copies keep two rows of each
+ * link and rebuild the third as conj(row0 x row1).  The caller may free U as
  * soon as the stream has passed this call.
  */
 int dw_load_gauge(dw_lattice *lat, const void *U, void *stream);

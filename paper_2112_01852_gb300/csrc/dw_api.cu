@@ -130,8 +130,8 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     memset(&p, 0, sizeof(p));
     p.out = (char *)out + (size_t)r0 * rhs_bytes;
     p.in = (const char *)in + (size_t)r0 * rhs_bytes;
-    p.gmain = lat->gmain[prec];
-    p.gtail = lat->gtail[prec];
+    p.gauge = lat->gauge[prec];
+    for (int m = 0; m < 4; ++m) p.bc[m] = lat->bc[m];
     for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
     p.V4 = (int)lat->V4;
     p.Ls = lat->Ls;
@@ -243,13 +243,10 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
   cudaGetDevice(&lat->device);
   cudaDeviceGetAttribute(&lat->num_sms, cudaDevAttrMultiProcessorCount, lat->device);
   for (int p = 0; p < 3; ++p) {
-    const int R = prec_reals_per_vec(p);
-    const size_t main_bytes = (size_t)4 * (16 / R) * V4 * prec_vec_bytes(p);
-    const size_t tail_bytes = (size_t)4 * V4 * 2 * prec_real_bytes(p);
-    cudaError_t e1 = cudaMalloc(&lat->gmain[p], main_bytes);
-    cudaError_t e2 = cudaMalloc(&lat->gtail[p], tail_bytes);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    const size_t bytes = (size_t)4 * prec_link_vecs(p) * lat->V4p * prec_vec_bytes(p);
+    if (cudaMalloc(&lat->gauge[p], bytes) != cudaSuccess) {
       cudaGetLastError();
+      lat->gauge[p] = nullptr;
       dw_destroy_lattice(lat);
       return fail(DW_ERR_ALLOC, "gauge allocation failed");
     }
@@ -260,10 +257,8 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
 
 void dw_destroy_lattice(dw_lattice *lat) {
   if (!lat) return;
-  for (int p = 0; p < 3; ++p) {
-    if (lat->gmain[p]) cudaFree(lat->gmain[p]);
-    if (lat->gtail[p]) cudaFree(lat->gtail[p]);
-  }
+  for (int p = 0; p < 3; ++p)
+    if (lat->gauge[p]) cudaFree(lat->gauge[p]);
   if (lat->scratch) cudaFree(lat->scratch);
   if (lat->stage_in) cudaFree(lat->stage_in);
   if (lat->stage_out) cudaFree(lat->stage_out);
@@ -278,7 +273,7 @@ int dw_load_gauge(dw_lattice *lat, const void *U, void *stream) {
   if (!U) return fail(DW_ERR_ARG, "U is NULL");
   if (!aligned16(U)) return fail(DW_ERR_ARG, "U must be 16-byte aligned");
   FieldGeom g = geom(lat);
-  if (load_gauge(g, lat->bc, U, lat->gmain, lat->gtail, (cudaStream_t)stream))
+  if (load_gauge(g, lat->bc, U, lat->gauge, (cudaStream_t)stream))
     return cuda_fail(cudaGetLastError(), "gauge conversion launch");
   lat->gauge_loaded = true;
   return DW_OK;
@@ -407,8 +402,8 @@ int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, 
   DslashParams p;
   memset(&p, 0, sizeof(p));
   p.in = in;
-  p.gmain = lat->gmain[lat->prec];
-  p.gtail = lat->gtail[lat->prec];
+  p.gauge = lat->gauge[lat->prec];
+  for (int m = 0; m < 4; ++m) p.bc[m] = lat->bc[m];
   for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
   p.V4 = (int)lat->V4;
   p.Ls = lat->Ls;

@@ -17,32 +17,37 @@ namespace dw {
 
 // ---------------------------------------------------------------------------
 // Precision traits.  A fermion plane element is one `vec`: 2 doubles (F64),
-// 4 floats (F32) or 4 halves (F16).  `C` is the arithmetic type.  Links keep
-// their first 16 reals in `vec` planes and the last 2 in a `tvec` plane.
+// 4 floats (F32) or 4 halves (F16).  `C` is the arithmetic type.
+// A link is NLV vecs: all 18 reals at FP64; at FP32 / FP16 only its first two
+// rows (12 reals), the third being rebuilt as conj(row0 x row1) (SU(3)).
 struct F64 {
   using vec = double2;
-  using tvec = double2;
   using C = double;
   static constexpr int R = 2;
   static constexpr int RB = 8;  // bytes per real
+  static constexpr int NLV = 9;
+  static constexpr bool LINK12 = false;
   static constexpr int id = DW_F64;
 };
 struct F32 {
   using vec = float4;
-  using tvec = float2;
   using C = float;
   static constexpr int R = 4;
   static constexpr int RB = 4;
+  static constexpr int NLV = 3;
+  static constexpr bool LINK12 = true;
   static constexpr int id = DW_F32;
 };
 struct F16 {
-  using vec = uint2;         // 4 x binary16
-  using tvec = unsigned int; // 2 x binary16
+  using vec = uint2;  // 4 x binary16
   using C = float;
   static constexpr int R = 4;
   static constexpr int RB = 2;
+  static constexpr int NLV = 3;
+  static constexpr bool LINK12 = true;
   static constexpr int id = DW_F16;
 };
+inline int prec_link_vecs(int prec) { return prec == DW_F64 ? 9 : 3; }
 
 inline int prec_vec_bytes(int prec) { return prec == DW_F64 ? 16 : (prec == DW_F32 ? 16 : 8); }
 inline int prec_reals_per_vec(int prec) { return prec == DW_F64 ? 2 : 4; }
@@ -70,17 +75,6 @@ __device__ __forceinline__ void widen(const uint2 &v, float *r) {
   r[2] = fb.x;
   r[3] = fb.y;
 }
-__device__ __forceinline__ void widen_t(const double2 &v, double *r) { widen(v, r); }
-__device__ __forceinline__ void widen_t(const float2 &v, float *r) {
-  r[0] = v.x;
-  r[1] = v.y;
-}
-__device__ __forceinline__ void widen_t(const unsigned int &v, float *r) {
-  __half2 a = *reinterpret_cast<const __half2 *>(&v);
-  float2 fa = __half22float2(a);
-  r[0] = fa.x;
-  r[1] = fa.y;
-}
 
 __device__ __forceinline__ double2 narrow_vec(const double *r, double2 *) {
   return make_double2(r[0], r[1]);
@@ -96,17 +90,6 @@ __device__ __forceinline__ uint2 narrow_vec(const float *r, uint2 *) {
   v.y = *reinterpret_cast<unsigned int *>(&b);
   return v;
 }
-__device__ __forceinline__ double2 narrow_tvec(const double *r, double2 *) {
-  return make_double2(r[0], r[1]);
-}
-__device__ __forceinline__ float2 narrow_tvec(const float *r, float2 *) {
-  return make_float2(r[0], r[1]);
-}
-__device__ __forceinline__ unsigned int narrow_tvec(const float *r, unsigned int *) {
-  __half2 a = __floats2half2_rn(r[0], r[1]);
-  return *reinterpret_cast<unsigned int *>(&a);
-}
-
 // Rounding straight from double (one rounding step, nearest even) for the
 // layout converters that read canonical FP64 data.
 __device__ __forceinline__ double2 narrow_from_f64(const double *r, double2 *) {
@@ -124,17 +107,6 @@ __device__ __forceinline__ uint2 narrow_from_f64(const double *r, uint2 *) {
   v.y = (unsigned)__half_as_ushort(h[2]) | ((unsigned)__half_as_ushort(h[3]) << 16);
   return v;
 }
-__device__ __forceinline__ double2 narrow_t_from_f64(const double *r, double2 *) {
-  return make_double2(r[0], r[1]);
-}
-__device__ __forceinline__ float2 narrow_t_from_f64(const double *r, float2 *) {
-  return make_float2((float)r[0], (float)r[1]);
-}
-__device__ __forceinline__ unsigned int narrow_t_from_f64(const double *r, unsigned int *) {
-  return (unsigned)__half_as_ushort(__double2half(r[0])) |
-         ((unsigned)__half_as_ushort(__double2half(r[1])) << 16);
-}
-
 template <class P>
 __device__ __forceinline__ void load_vec(typename P::C *r, const typename P::vec *p) {
   widen(__ldg(p), r);
@@ -157,6 +129,11 @@ __host__ __device__ __forceinline__ long long site_off(int x4, int s, int Ls, in
   return ((long long)(x4 >> 5) * Ls + s) * npv * 32 + (x4 & 31);
 }
 __host__ __device__ __forceinline__ long long padded_v4(long long V4) { return (V4 + 31) / 32 * 32; }
+// Gauge field, blocked the same way: vec k of link U_mu(x4) is at
+// (((x4/32)*4 + mu)*nlv + k)*32 + x4%32.
+__host__ __device__ __forceinline__ long long link_off(int x4, int mu, int nlv) {
+  return (((long long)(x4 >> 5) * 4 + mu) * nlv) * 32 + (x4 & 31);
+}
 
 // ---------------------------------------------------------------------------
 // Operator kinds handled by the stencil kernel.
@@ -165,14 +142,14 @@ enum OpKind { OP_DHOP = 0, OP_DHOP_DAG = 1, OP_D = 2, OP_DDAG = 3 };
 struct DslashParams {
   void *out;
   const void *in;
-  const void *gmain;  // [mu][16/R][V4] vec
-  const void *gtail;  // [mu][V4] tvec
+  const void *gauge;  // blocked links at this precision (see link_off)
   int L[4];
   int V4;
   int Ls;
   long long plane;       // vecs between consecutive planes of one site (kPlaneStride)
   long long rhs_stride;  // vecs per right-hand side (= padded V4 * Ls * 24/R)
   int nrhs;             // right-hand sides in this launch (<= kMaxRhsPerLaunch)
+  int bc[4];            // boundary signs (the rebuilt third row of a 12-real link needs them)
   const int *gate;      // optional: CTAs of RHS r run only if gate[r * gate_stride] != 0
   int gate_stride;
   const void *halo_up;  // optional t-face halves from the rank above (variant 0 only)
@@ -227,9 +204,8 @@ struct dw_lattice {
   int device;
   int num_sms;
   bool gauge_loaded;
-  // gauge copies per precision: main planes and tail plane
-  void *gmain[3];
-  void *gtail[3];
+  // gauge copies per precision (blocked; 18 reals per link at FP64, 12 below)
+  void *gauge[3];
   // scratch: one field for D^+D, host-apply staging, reduction partials
   void *scratch;
   size_t scratch_bytes;

@@ -248,15 +248,30 @@ __device__ __forceinline__ void store_spinor(typename P::vec *base, long long pl
   }
 }
 
+// Third row of an SU(3) link from the first two: row2 = sign * conj(row0 x row1).
+// The stored rows carry the boundary sign of a link that crosses the lattice
+// edge; the cross product cancels it, so `sign` puts it back.
+template <class C>
+__device__ __forceinline__ void rebuild_row2(C *U, C sign) {
+  const C a0r = U[0], a0i = U[1], a1r = U[2], a1i = U[3], a2r = U[4], a2i = U[5];
+  const C b0r = U[6], b0i = U[7], b1r = U[8], b1i = U[9], b2r = U[10], b2i = U[11];
+  U[12] = sign * ((a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i));
+  U[13] = -sign * ((a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r));
+  U[14] = sign * ((a2r * b0r - a2i * b0i) - (a0r * b2r - a0i * b2i));
+  U[15] = -sign * ((a2r * b0i + a2i * b0r) - (a0r * b2i + a0i * b2r));
+  U[16] = sign * ((a0r * b1r - a0i * b1i) - (a1r * b0r - a1i * b0i));
+  U[17] = -sign * ((a0r * b1i + a0i * b1r) - (a1r * b0i + a1i * b0r));
+}
+
+// U_mu(x4) into 18 reals (row, col, re/im); `sign` is the boundary sign of
+// this link (used only to rebuild the third row of a 12-real link).
 template <class P>
-__device__ __forceinline__ void load_link(typename P::C *U, const typename P::vec *gmain,
-                                          const typename P::tvec *gtail, int mu, int x4,
-                                          int V4) {
-  constexpr int NM = 16 / P::R;
-  const typename P::vec *p = gmain + (long long)mu * NM * V4 + x4;
+__device__ __forceinline__ void load_link(typename P::C *U, const typename P::vec *gauge, int mu,
+                                          int x4, typename P::C sign) {
+  const typename P::vec *p = gauge + link_off(x4, mu, P::NLV);
 #pragma unroll
-  for (int q = 0; q < NM; ++q) widen(__ldg(p + (long long)q * V4), U + q * P::R);
-  widen_t(__ldg(gtail + (long long)mu * V4 + x4), U + 16);
+  for (int k = 0; k < P::NLV; ++k) widen(__ldg(p + k * 32), U + k * P::R);
+  if (P::LINK12) rebuild_row2(U, sign);
 }
 
 template <class V2>
@@ -325,14 +340,13 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
 // itself (PHI = false) or phi = (b + cK) psi (PHI = true).
 template <class P, int MU, int S, bool ADJ, bool PHI, bool FIRST, int SPT>
 __device__ __forceinline__ void hop_dir(Spinor<typename Pair<P>::type> (&acc)[SPT],
-                                        const Field<P> &F, const typename P::vec *gmain,
-                                        const typename P::tvec *gtail, int y4, int l4, int s0,
-                                        int Ls, typename P::C b, typename P::C c,
-                                        typename P::C mf) {
+                                        const Field<P> &F, const typename P::vec *gauge,
+                                        typename P::C lsign, int y4, int l4, int s0, int Ls,
+                                        typename P::C b, typename P::C c, typename P::C mf) {
   using C = typename P::C;
   using V2 = typename Pair<P>::type;
   C U[18];
-  load_link<P>(U, gmain, gtail, MU, l4, F.V4);
+  load_link<P>(U, gauge, MU, l4, lsign);
   auto body = [&](int j, const Spinor<V2> &v) {
     Half<V2> h, w;
     project<MU, S>(h, v.up, v.lo);
@@ -383,13 +397,13 @@ __device__ __forceinline__ void cp_async_wait() {
 template <class P, bool PHI, int SPT>
 struct StageLayout {
   static constexpr int VPQ = 4 / P::R;
-  static constexpr int NM = 16 / P::R;  // link vec planes
+  static constexpr int NM = P::NLV;  // link vecs
   // spinor vec slots per direction: full spinors (Dhop) or the halves that the
   // rolling (b + cK) combination needs: upper s0-1 .. s0+SPT-1, lower s0 .. s0+SPT
   static constexpr int NSP = PHI ? 6 * (SPT + 1) * VPQ : 6 * SPT * VPQ;
   static constexpr int NVEC = NSP + NM;
   static __host__ __device__ size_t stage_bytes(int T) {
-    size_t b = (size_t)NVEC * T * sizeof(typename P::vec) + (size_t)T * sizeof(typename P::tvec);
+    size_t b = (size_t)NVEC * T * sizeof(typename P::vec);
     return (b + 15) & ~(size_t)15;
   }
 };
@@ -398,7 +412,6 @@ template <class P, int OP, int SPT>
 struct StagedHop {
   using C = typename P::C;
   using vec = typename P::vec;
-  using tvec = typename P::tvec;
   using V2 = typename Pair<P>::type;
   static constexpr bool PHI = (OP == OP_D);
   using L = StageLayout<P, PHI, SPT>;
@@ -408,17 +421,11 @@ struct StagedHop {
   __device__ __forceinline__ vec *vslot(int stage, int k) const {
     return reinterpret_cast<vec *>(smem + (size_t)stage * L::stage_bytes(T)) + (size_t)k * T + t;
   }
-  __device__ __forceinline__ tvec *tslot(int stage) const {
-    return reinterpret_cast<tvec *>(smem + (size_t)stage * L::stage_bytes(T) +
-                                    (size_t)L::NVEC * T * sizeof(vec)) + t;
-  }
-  __device__ __forceinline__ void issue(int stage, const Field<P> &F, const vec *gmain,
-                                        const tvec *gtail, int mu, int y4, int l4, int s0,
-                                        int Ls) const {
-    const vec *lp = gmain + (long long)mu * L::NM * F.V4 + l4;
+  __device__ __forceinline__ void issue(int stage, const Field<P> &F, const vec *gauge, int mu,
+                                        int y4, int l4, int s0, int Ls) const {
+    const vec *lp = gauge + link_off(l4, mu, P::NLV);
 #pragma unroll
-    for (int q = 0; q < L::NM; ++q) cp_async<sizeof(vec)>(vslot(stage, L::NSP + q), lp + (long long)q * F.V4);
-    cp_async<sizeof(tvec)>(tslot(stage), gtail + (long long)mu * F.V4 + l4);
+    for (int q = 0; q < L::NM; ++q) cp_async<sizeof(vec)>(vslot(stage, L::NSP + q), lp + q * 32);
     if (!PHI) {
 #pragma unroll
       for (int j = 0; j < SPT; ++j) {
@@ -464,10 +471,10 @@ struct StagedHop {
     re = *reinterpret_cast<const double2 *>(vslot(stage, k));
     im = *reinterpret_cast<const double2 *>(vslot(stage, k + 1));
   }
-  __device__ __forceinline__ void read_link(C *U, int stage) const {
+  __device__ __forceinline__ void read_link(C *U, int stage, C sign) const {
 #pragma unroll
     for (int q = 0; q < L::NM; ++q) widen(*vslot(stage, L::NSP + q), U + q * P::R);
-    widen_t(*tslot(stage), U + 16);
+    if (P::LINK12) rebuild_row2(U, sign);
   }
 };
 
@@ -476,9 +483,9 @@ struct StagedHop {
 template <class P, int OP, int SPT>
 __device__ __forceinline__ void hop_staged(Spinor<typename Pair<P>::type> (&acc)[SPT],
                                            const StagedHop<P, OP, SPT> &H, const Field<P> &F,
-                                           const typename P::vec *gmain,
-                                           const typename P::tvec *gtail, int x4, bool active,
-                                           const int (&nb)[8], int s0, int Ls,
+                                           const typename P::vec *gauge, int x4, bool active,
+                                           const int (&nb)[8], const int (&lsg)[8], int s0,
+                                           int Ls,
                                            typename P::C b, typename P::C c, typename P::C mf) {
   using C = typename P::C;
   using V2 = typename Pair<P>::type;
@@ -489,21 +496,21 @@ __device__ __forceinline__ void hop_staged(Spinor<typename Pair<P>::type> (&acc)
   // direction d: mu = 3 - d/2; even d forward (link at x4), odd d backward
 #pragma unroll
   for (int d = 0; d < kStages - 1; ++d) {
-    if (active) H.issue(d % kStages, F, gmain, gtail, 3 - d / 2, nb[d], (d & 1) ? nb[d] : x4, s0, Ls);
+    if (active) H.issue(d % kStages, F, gauge, 3 - d / 2, nb[d], (d & 1) ? nb[d] : x4, s0, Ls);
     cp_async_commit();
   }
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
     const int dn = d + kStages - 1;
     if (dn < 8 && active)
-      H.issue(dn % kStages, F, gmain, gtail, 3 - dn / 2, nb[dn < 8 ? dn : 0],
+      H.issue(dn % kStages, F, gauge, 3 - dn / 2, nb[dn < 8 ? dn : 0],
               (dn & 1) ? nb[dn < 8 ? dn : 0] : x4, s0, Ls);
     cp_async_commit();
     cp_async_wait<kStages - 1>();
     if (!active) continue;
     const int stg = d % kStages;
     C U[18];
-    H.read_link(U, stg);
+    H.read_link(U, stg, (C)lsg[d]);
     auto body = [&](int j, const Spinor<V2> &v) {
       Half<V2> h, w;
       switch (d) {
@@ -553,9 +560,9 @@ __device__ __forceinline__ void hop_staged(Spinor<typename Pair<P>::type> (&acc)
 // behind the arithmetic.  ORDER 0 visits t, z, y, x; ORDER 1 visits x, y, z, t.
 template <class P, int SPT, int ORDER, bool DAG>
 __device__ __forceinline__ void hop_prefetch(Spinor<typename Pair<P>::type> (&acc)[SPT],
-                                             const Field<P> &F, const typename P::vec *gmain,
-                                             const typename P::tvec *gtail, int x4,
-                                             const int (&nb)[8], int s0) {
+                                             const Field<P> &F, const typename P::vec *gauge,
+                                             int x4, const int (&nb)[8], const int (&lsg)[8],
+                                             int s0) {
   using C = typename P::C;
   using V2 = typename Pair<P>::type;
   constexpr int SF = DAG ? 1 : -1;
@@ -563,11 +570,12 @@ __device__ __forceinline__ void hop_prefetch(Spinor<typename Pair<P>::type> (&ac
   constexpr int N = 8 * SPT;
   auto mu_of = [](int d) { return ORDER == 0 ? 3 - d / 2 : d / 2; };
   auto nb_of = [&](int d) { return nb[(3 - mu_of(d)) * 2 + (d & 1)]; };
+  auto sg_of = [&](int d) { return (C)lsg[(3 - mu_of(d)) * 2 + (d & 1)]; };
   Spinor<V2> nxt;
   C Unxt[18];
   F.load_half(nxt.up, nb_of(0), s0, 0);
   F.load_half(nxt.lo, nb_of(0), s0, 1);
-  load_link<P>(Unxt, gmain, gtail, mu_of(0), x4, F.V4);
+  load_link<P>(Unxt, gauge, mu_of(0), x4, sg_of(0));
   C U[18];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
@@ -581,7 +589,8 @@ __device__ __forceinline__ void hop_prefetch(Spinor<typename Pair<P>::type> (&ac
       const int d1 = (k + 1) / SPT, j1 = (k + 1) % SPT;
       F.load_half(nxt.up, nb_of(d1), s0 + j1, 0);
       F.load_half(nxt.lo, nb_of(d1), s0 + j1, 1);
-      if (j1 == 0) load_link<P>(Unxt, gmain, gtail, mu_of(d1), (d1 & 1) ? nb_of(d1) : x4, F.V4);
+      if (j1 == 0)
+        load_link<P>(Unxt, gauge, mu_of(d1), (d1 & 1) ? nb_of(d1) : x4, sg_of(d1));
     }
     Half<V2> h, w;
     const int mu = mu_of(d);
@@ -626,14 +635,13 @@ __device__ __forceinline__ void hop_prefetch(Spinor<typename Pair<P>::type> (&ac
 template <class P, int S, bool FIRST, int SPT>
 __device__ __forceinline__ void halo_hop_up(Spinor<typename Pair<P>::type> (&acc)[SPT],
                                             const typename P::vec *halo, long long hplane,
-                                            int Vf, int face, const typename P::vec *gmain,
-                                            const typename P::tvec *gtail, int x4, int V4,
-                                            int s0) {
+                                            int Vf, int face, const typename P::vec *gauge,
+                                            int x4, typename P::C lsign, int s0) {
   using C = typename P::C;
   using V2 = typename Pair<P>::type;
   constexpr int VPQ = 4 / P::R;
   C U[18];
-  load_link<P>(U, gmain, gtail, 3, x4, V4);
+  load_link<P>(U, gauge, 3, x4, lsign);
 #pragma unroll
   for (int j = 0; j < SPT; ++j) {
     Half<V2> h, w;
@@ -666,8 +674,8 @@ __device__ __forceinline__ void halo_hop_down(Spinor<typename Pair<P>::type> (&a
 // projection of its last t slice.  One thread per (face site, s) of one RHS.
 template <class P, bool DAG>
 __global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send_up,
-                                 const typename P::vec *in, const typename P::vec *gmain,
-                                 const typename P::tvec *gtail, int V4, int Vf, int Lt, int Ls,
+                                 const typename P::vec *in, const typename P::vec *gauge,
+                                 int bct, int V4, int Vf, int Lt, int Ls,
                                  long long plane, long long rhs_stride, long long hplane,
                                  long long hrhs) {
   using C = typename P::C;
@@ -703,7 +711,7 @@ __global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send
     Half<V2> h, w;
     project<3, SB>(h, v.up, v.lo);
     C U[18];
-    load_link<P>(U, gmain, gtail, 3, x4, V4);
+    load_link<P>(U, gauge, 3, x4, (C)bct);  // the last slice's t link crosses the edge
     su3_mul<true>(w, U, h);
     typename P::vec *o = send_up + (long long)rhs * hrhs + (long long)s * Vf + face;
 #pragma unroll
@@ -720,15 +728,14 @@ int launch_halo_pack_impl(const DslashParams &p, void *send_dn, void *send_up, i
   const int tpb = 128;
   dim3 grid((unsigned)(((long long)Vf * p.Ls + tpb - 1) / tpb), p.nrhs);
   using vec = typename P::vec;
-  using tvec = typename P::tvec;
   if (dag)
     halo_pack_kernel<P, true><<<grid, tpb, 0, st>>>(
-        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gmain,
-        (const tvec *)p.gtail, p.V4, Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
+        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gauge, p.bc[3], p.V4,
+        Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
   else
     halo_pack_kernel<P, false><<<grid, tpb, 0, st>>>(
-        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gmain,
-        (const tvec *)p.gtail, p.V4, Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
+        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gauge, p.bc[3], p.V4,
+        Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -736,7 +743,6 @@ template <class P, int OP, int SPT, int VAR>
 __global__ void dslash_kernel(const DslashParams p) {
   using C = typename P::C;
   using vec = typename P::vec;
-  using tvec = typename P::tvec;
   using V2 = typename Pair<P>::type;
   constexpr bool DAG = (OP == OP_DHOP_DAG || OP == OP_DDAG);
   constexpr bool PHI = (OP == OP_D);
@@ -776,8 +782,7 @@ __global__ void dslash_kernel(const DslashParams p) {
   F.V4 = p.V4;
   F.Ls = p.Ls;
   vec *out = reinterpret_cast<vec *>(p.out) + (long long)rhs * p.rhs_stride;
-  const vec *gmain = reinterpret_cast<const vec *>(p.gmain);
-  const tvec *gtail = reinterpret_cast<const tvec *>(p.gtail);
+  const vec *gauge = reinterpret_cast<const vec *>(p.gauge);
 
   const C mf = (OP == OP_D || OP == OP_DDAG) ? (C)p.mf[rhs] : C(0);
   const C b = (C)p.b, c = (C)p.c;
@@ -788,7 +793,8 @@ __global__ void dslash_kernel(const DslashParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t smem_used = 0;
 
-  int nb[8];  // neighbours in the order t+, t-, z+, z-, y+, y-, x+, x-
+  int nb[8];   // neighbours in the order t+, t-, z+, z-, y+, y-, x+, x-
+  int lsg[8];  // boundary sign of the link each of those hops uses
   if (active) {
     int rem = x4;
     const int cx = rem % p.L[0];
@@ -808,9 +814,20 @@ __global__ void dslash_kernel(const DslashParams p) {
     nb[3] = (cz == 0) ? x4 + (p.L[2] - 1) * st2 : x4 - st2;
     nb[0] = (ct == p.L[3] - 1) ? x4 - (p.L[3] - 1) * st3 : x4 + st3;
     nb[1] = (ct == 0) ? x4 + (p.L[3] - 1) * st3 : x4 - st3;
+    lsg[0] = (ct == p.L[3] - 1) ? p.bc[3] : 1;
+    lsg[1] = (ct == 0) ? p.bc[3] : 1;
+    lsg[2] = (cz == p.L[2] - 1) ? p.bc[2] : 1;
+    lsg[3] = (cz == 0) ? p.bc[2] : 1;
+    lsg[4] = (cy == p.L[1] - 1) ? p.bc[1] : 1;
+    lsg[5] = (cy == 0) ? p.bc[1] : 1;
+    lsg[6] = (cx == p.L[0] - 1) ? p.bc[0] : 1;
+    lsg[7] = (cx == 0) ? p.bc[0] : 1;
   } else {
 #pragma unroll
-    for (int d = 0; d < 8; ++d) nb[d] = 0;
+    for (int d = 0; d < 8; ++d) {
+      nb[d] = 0;
+      lsg[d] = 1;
+    }
   }
 
   if (VAR == 0) {
@@ -822,41 +839,41 @@ __global__ void dslash_kernel(const DslashParams p) {
       const long long hrhs = hplane * (12 / P::R);
       if (p.halo_up && ct == p.L[3] - 1)
         halo_hop_up<P, SF, true, SPT>(acc, (const vec *)p.halo_up + rhs * hrhs, hplane, Vf,
-                                      x4 - ct * Vf, gmain, gtail, x4, p.V4, s0);
+                                      x4 - ct * Vf, gauge, x4, (C)lsg[0], s0);
       else
-        hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gmain, gtail, nb[0], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gauge, (C)lsg[0], nb[0], x4, s0, Ls, b, c, mf);
       if (p.halo_dn && ct == 0)
         halo_hop_down<P, SB, SPT>(acc, (const vec *)p.halo_dn + rhs * hrhs, hplane, Vf, x4, s0);
       else
-        hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[1], nb[1], s0, Ls, b, c, mf);
-      hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[2], x4, s0, Ls, b, c, mf);
-      hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[3], nb[3], s0, Ls, b, c, mf);
-      hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[4], x4, s0, Ls, b, c, mf);
-      hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[5], nb[5], s0, Ls, b, c, mf);
-      hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[6], x4, s0, Ls, b, c, mf);
-      hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[7], nb[7], s0, Ls, b, c, mf);
+        hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[1], nb[1], nb[1], s0, Ls, b, c, mf);
+      hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[2], nb[2], x4, s0, Ls, b, c, mf);
+      hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[3], nb[3], nb[3], s0, Ls, b, c, mf);
+      hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[4], nb[4], x4, s0, Ls, b, c, mf);
+      hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[5], nb[5], nb[5], s0, Ls, b, c, mf);
+      hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[6], nb[6], x4, s0, Ls, b, c, mf);
+      hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[7], nb[7], nb[7], s0, Ls, b, c, mf);
     }
   } else if (VAR >= 2) {
     if (PHI) {  // the (b + cK) input combination keeps the VAR 0 path
       if (active) {
-        hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gmain, gtail, nb[0], x4, s0, Ls, b, c, mf);
-        hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[1], nb[1], s0, Ls, b, c, mf);
-        hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[2], x4, s0, Ls, b, c, mf);
-        hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[3], nb[3], s0, Ls, b, c, mf);
-        hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[4], x4, s0, Ls, b, c, mf);
-        hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[5], nb[5], s0, Ls, b, c, mf);
-        hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gmain, gtail, nb[6], x4, s0, Ls, b, c, mf);
-        hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gmain, gtail, nb[7], nb[7], s0, Ls, b, c, mf);
+        hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gauge, (C)lsg[0], nb[0], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[1], nb[1], nb[1], s0, Ls, b, c, mf);
+        hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[2], nb[2], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[3], nb[3], nb[3], s0, Ls, b, c, mf);
+        hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[4], nb[4], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[5], nb[5], nb[5], s0, Ls, b, c, mf);
+        hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[6], nb[6], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[7], nb[7], nb[7], s0, Ls, b, c, mf);
       }
     } else if (active) {
-      hop_prefetch<P, SPT, VAR == 2 ? 0 : 1, DAG>(acc, F, gmain, gtail, x4, nb, s0);
+      hop_prefetch<P, SPT, VAR == 2 ? 0 : 1, DAG>(acc, F, gauge, x4, nb, lsg, s0);
     }
   } else {
     StagedHop<P, OP, SPT> H;
     H.smem = smem_raw;
     H.T = tx * nchunk;
     H.t = chunk * tx + threadIdx.x;
-    hop_staged<P, OP, SPT>(acc, H, F, gmain, gtail, x4, active, nb, s0, Ls, b, c, mf);
+    hop_staged<P, OP, SPT>(acc, H, F, gauge, x4, active, nb, lsg, s0, Ls, b, c, mf);
     smem_used = kStages * StageLayout<P, PHI, SPT>::stage_bytes(H.T);
   }
 

@@ -97,24 +97,20 @@ int unpack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int
 }
 
 // ---------------------------------------------------------------------------
-// Gauge: canonical complex128 [x4][mu][row][col] -> per precision main planes
-// [mu][16/R][V4] + tail plane [mu][V4].  A link U_mu(x) with x_mu = L_mu - 1
-// crosses the lattice edge and is multiplied by bc[mu].
+// Gauge: canonical complex128 [x4][mu][row][col] -> per precision blocked links
+// (link_off): all 18 reals at F64, the first two rows (12 reals) at F32 / F16.
+// A link U_mu(x) with x_mu = L_mu - 1 crosses the lattice edge and is
+// multiplied by bc[mu].
 template <class P>
-__device__ __forceinline__ void store_link(void *gmain, void *gtail, int mu, int x4, int V4,
-                                          const double *u) {
-  constexpr int NM = 16 / P::R;
-  typename P::vec *m = (typename P::vec *)gmain + (long long)mu * NM * V4 + x4;
+__device__ __forceinline__ void store_link(void *gauge, int mu, int x4, const double *u) {
+  typename P::vec *m = (typename P::vec *)gauge + link_off(x4, mu, P::NLV);
 #pragma unroll
-  for (int q = 0; q < NM; ++q)
-    m[(long long)q * V4] = narrow_from_f64(u + q * P::R, (typename P::vec *)nullptr);
-  ((typename P::tvec *)gtail)[(long long)mu * V4 + x4] =
-      narrow_t_from_f64(u + 16, (typename P::tvec *)nullptr);
+  for (int q = 0; q < P::NLV; ++q)
+    m[q * 32] = narrow_from_f64(u + q * P::R, (typename P::vec *)nullptr);
 }
 
 __global__ void gauge_kernel(const double *U, int L0, int L1, int L2, int L3, int bc0, int bc1,
-                             int bc2, int bc3, void *m64, void *t64, void *m32, void *t32,
-                             void *m16, void *t16) {
+                             int bc2, int bc3, void *g64, void *g32, void *g16) {
   const long long V4 = (long long)L0 * L1 * L2 * L3;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= 4 * V4) return;
@@ -135,18 +131,18 @@ __global__ void gauge_kernel(const double *U, int L0, int L1, int L2, int L3, in
   const double *src = U + ((long long)x4 * 4 + mu) * 18;
 #pragma unroll
   for (int k = 0; k < 18; ++k) u[k] = f * src[k];
-  store_link<F64>(m64, t64, mu, x4, (int)V4, u);
-  store_link<F32>(m32, t32, mu, x4, (int)V4, u);
-  store_link<F16>(m16, t16, mu, x4, (int)V4, u);
+  store_link<F64>(g64, mu, x4, u);
+  store_link<F32>(g32, mu, x4, u);
+  store_link<F16>(g16, mu, x4, u);
 }
 
-int load_gauge(const FieldGeom &g, const int bc[4], const void *U, void *const gmain[3],
-               void *const gtail[3], cudaStream_t st) {
+int load_gauge(const FieldGeom &g, const int bc[4], const void *U, void *const gauge[3],
+               cudaStream_t st) {
   const long long n = 4LL * g.V4;
   const int tpb = 256;
   gauge_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-      (const double *)U, g.L[0], g.L[1], g.L[2], g.L[3], bc[0], bc[1], bc[2], bc[3], gmain[0],
-      gtail[0], gmain[1], gtail[1], gmain[2], gtail[2]);
+      (const double *)U, g.L[0], g.L[1], g.L[2], g.L[3], bc[0], bc[1], bc[2], bc[3], gauge[0],
+      gauge[1], gauge[2]);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

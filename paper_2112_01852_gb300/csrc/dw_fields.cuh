@@ -19,8 +19,8 @@ int pack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int n
 int unpack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int nrhs,
                    cudaStream_t st);
 // canonical gauge (device) -> internal links at F64, F32 and F16
-int load_gauge(const FieldGeom &g, const int bc[4], const void *U, void *const gmain[3],
-               void *const gtail[3], cudaStream_t st);
+int load_gauge(const FieldGeom &g, const int bc[4], const void *U, void *const gauge[3],
+               cudaStream_t st);
 // internal field precision conversion
 int convert_fermion(const FieldGeom &g, int pi, int po, void *dst, const void *src, int nrhs,
                     cudaStream_t st);
