@@ -119,9 +119,16 @@ size_t halo_bytes(const dw_lattice *lat, int prec, int nrhs) {
          prec_real_bytes(prec) * (size_t)nrhs;
 }
 
+// CTAs per right-hand side of a stencil launch with tile `t`.
+long long dslash_ctas_per_rhs(const dw_lattice *lat, TileConfig t) {
+  const long long per_plane = ((long long)lat->dims[0] * lat->dims[1] + t.tx - 1) / t.tx;
+  return per_plane * lat->dims[2] * lat->dims[3];
+}
+
 int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
-               const int *gate, int gate_stride, const void *halo_up, const void *halo_dn) {
+               const int *gate, int gate_stride, const void *halo_up, const void *halo_dn,
+               double *norm_partials) {
   const size_t rhs_bytes = field_bytes(lat, prec, 1);
   const size_t hrhs_bytes = halo_bytes(lat, prec, 1);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
@@ -147,6 +154,8 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.c = lat->c;
     for (int r = 0; r < n; ++r) p.mf[r] = mf_host ? mf_host[r0 + r] : 0.0;
     const TileConfig cfg = force ? *force : pick_tile(lat, prec, op, nrhs);
+    p.norm_partials =
+        norm_partials ? norm_partials + (size_t)r0 * dslash_ctas_per_rhs(lat, cfg) : nullptr;
     const int rc = launch_dslash(p, prec, op, cfg, st);
     if (rc == -2)
       return fail(DW_ERR_ARG, "unsupported tile (spt=%d, tx=%d, variant=%d, zblk=%d) for Ls=%d",
@@ -357,7 +366,7 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d for Ls=%d Lz=%d (slices per thread "
-                "must divide Ls, tx a multiple of 32, variant 0..3, zblk dividing Lz, CTA within "
+                "must divide Ls, tx a multiple of 32, variant 0..4, zblk dividing Lz, CTA within "
                 "the kernel's limits)",
                 spt, tx, variant, zblk, lat->Ls, lat->dims[2]);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;

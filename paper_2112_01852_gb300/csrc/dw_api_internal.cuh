@@ -23,11 +23,15 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
 // NULL for the hopping-only kinds; `force` overrides the tile choice.
 // `gate` (optional) skips the CTAs of RHS r unless gate[r * gate_stride] != 0;
 // halo_up / halo_dn (optional, variant 0 tiles only) replace the t-neighbours
-// at the t faces of a decomposed sub-lattice.
+// at the t faces of a decomposed sub-lattice; norm_partials (optional, OP_D
+// only) receives |out|^2 per CTA, [rhs][dslash_ctas_per_rhs].
 int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
                const int *gate = nullptr, int gate_stride = 0, const void *halo_up = nullptr,
-               const void *halo_dn = nullptr);
+               const void *halo_dn = nullptr, double *norm_partials = nullptr);
+// CTAs per right-hand side of a stencil launch with tile `t` (the length of the
+// per-RHS rows of norm_partials).
+long long dslash_ctas_per_rhs(const dw_lattice *lat, TileConfig t);
 size_t halo_bytes(const dw_lattice *lat, int prec, int nrhs);
 int apply_op(dw_lattice *lat, int op, void *out, const void *in, const double *mf, int nrhs,
              cudaStream_t st);

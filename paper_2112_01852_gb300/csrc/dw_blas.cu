@@ -487,8 +487,8 @@ int cg_direction(const BlasCtx &c, int pp, int pr, void *p, const void *r_s, con
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int cg_alpha(const BlasCtx &c, const double *partial, CGState *st, cudaStream_t s) {
-  cg_alpha_kernel<<<c.nrhs, 32, 0, s>>>(partial, c.nblk, st);
+int cg_alpha(const BlasCtx &c, const double *partial, int nblk, CGState *st, cudaStream_t s) {
+  cg_alpha_kernel<<<c.nrhs, 32, 0, s>>>(partial, nblk, st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

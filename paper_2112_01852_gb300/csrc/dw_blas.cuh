@@ -61,7 +61,8 @@ int cg_update(const BlasCtx &c, int pp, int pr, void *x_s, void *r_s, const void
               const void *Ap, double *partial, const CGState *st, cudaStream_t s);
 int cg_direction(const BlasCtx &c, int pp, int pr, void *p, const void *r_s, const CGState *st,
                  cudaStream_t s);
-int cg_alpha(const BlasCtx &c, const double *partial, CGState *st, cudaStream_t s);
+// alpha = rr / <p, Ap> with <p, Ap> summed from nblk partials per RHS.
+int cg_alpha(const BlasCtx &c, const double *partial, int nblk, CGState *st, cudaStream_t s);
 int cg_beta(const BlasCtx &c, const double *partial, CGState *st, double delta, double tol,
             int maxit, cudaStream_t s);
 int cg_reliable(const BlasCtx &c, const double *partial, CGState *st, double tol, int maxit,

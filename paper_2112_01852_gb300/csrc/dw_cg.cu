@@ -38,6 +38,8 @@ struct CGWork {
   size_t partials_cap = 0;
   double *sums = nullptr;
   size_t sums_cap = 0;
+  double *dnorm = nullptr;  // |D p|^2 per stencil CTA
+  size_t dnorm_cap = 0;
   CGState *state = nullptr;
   size_t state_cap = 0;
   cudaStream_t stream = nullptr;
@@ -47,7 +49,7 @@ void cg_release(dw_lattice *lat) {
   CGWork *w = lat->cg;
   if (!w) return;
   void *bufs[] = {w->r64, w->Ax64, w->tmp64, w->p, w->Ap, w->tmp, w->rs, w->xs,
-                  w->partials, w->sums, w->state};
+                  w->partials, w->sums, w->dnorm, w->state};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (w->stream) cudaStreamDestroy(w->stream);
@@ -73,16 +75,17 @@ struct Solve {
   const int *gate_run() const { return &w->state[0].run; }
   const int *gate_update() const { return &w->state[0].need_update; }
 
-  // One inner iteration over all RHS (masked by `run`).
+  // One inner iteration over all RHS (masked by `run`).  <p, D^+D p> is
+  // |D p|^2, summed per CTA by the D pass itself.
   int iteration() {
+    const int nd = (int)dslash_ctas_per_rhs(lat, pick_tile(lat, pp, OP_D, nrhs));
     int rc = run_dslash(lat, pp, OP_D, w->tmp, w->p, mf, nrhs, st, nullptr, gate_run(),
-                        kCGStateInts);
+                        kCGStateInts, nullptr, nullptr, w->dnorm);
     if (rc) return rc;
     rc = run_dslash(lat, pp, OP_DDAG, w->Ap, w->tmp, mf, nrhs, st, nullptr, gate_run(),
                     kCGStateInts);
     if (rc) return rc;
-    if (blas_redot(c, pp, w->p, pp, w->Ap, w->partials, w->state, st) ||
-        cg_alpha(c, w->partials, w->state, st) ||
+    if (cg_alpha(c, w->dnorm, nd, w->state, st) ||
         cg_update(c, pp, pr, w->xs, w->rs, w->p, w->Ap, w->partials, w->state, st) ||
         cg_beta(c, w->partials, w->state, delta, tol, maxit, st) ||
         cg_direction(c, pp, pr, w->p, w->rs, w->state, st))
@@ -202,6 +205,12 @@ extern "C" int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double
     if (!lat->tuned.count(std::make_tuple(S.pp, op, nrhs)) &&
         (rc = tune_tile(lat, S.pp, op, nrhs, st, true)))
       return rc;
+
+  {
+    const long long nd = dslash_ctas_per_rhs(lat, pick_tile(lat, S.pp, OP_D, nrhs));
+    if ((rc = ensure((void **)&w->dnorm, &w->dnorm_cap, sizeof(double) * (size_t)nd * nrhs)))
+      return rc;
+  }
 
   // initial residual
   if ((rc = S.reliable(x, b, 1))) return rc;

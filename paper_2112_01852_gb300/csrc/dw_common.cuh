@@ -152,6 +152,7 @@ struct DslashParams {
   int bc[4];            // boundary signs (the rebuilt third row of a 12-real link needs them)
   const int *gate;      // optional: CTAs of RHS r run only if gate[r * gate_stride] != 0
   int gate_stride;
+  double *norm_partials;  // optional (OP_D): |out|^2 per CTA at [rhs][CTA index in the RHS]
   const void *halo_up;  // optional t-face halves from the rank above (variant 0 only)
   const void *halo_dn;  // optional t-face halves from the rank below (variant 0 only)
   int tiles_per_plane;  // set by the launcher: CTAs per (x, y) plane
@@ -169,7 +170,7 @@ struct TileConfig {
   int variant;  // hop-phase load scheme, 0 .. kNumVariants-1 (see dw.h)
   int zblk;     // z-blocks of the CTA traversal order (divides Lz)
 };
-constexpr int kNumVariants = 4;
+constexpr int kNumVariants = 5;
 
 // Stencil launch at precision `prec`: 0 on success, -2 for a tile/variant
 // that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA

@@ -739,8 +739,16 @@ int launch_halo_pack_impl(const DslashParams &p, void *send_dn, void *send_up, i
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Variant 4 is variant 0 compiled for at most 192 threads per CTA and three
+// resident CTAs per SM (a register cap that trades spills for occupancy).
+template <int VAR>
+struct LaunchBound {
+  static constexpr int threads = VAR == 4 ? 192 : 1024;
+  static constexpr int blocks = VAR == 4 ? 3 : 1;
+};
+
 template <class P, int OP, int SPT, int VAR>
-__global__ void dslash_kernel(const DslashParams p) {
+__device__ __forceinline__ void dslash_body(const DslashParams &p) {
   using C = typename P::C;
   using vec = typename P::vec;
   using V2 = typename Pair<P>::type;
@@ -830,7 +838,7 @@ __global__ void dslash_kernel(const DslashParams p) {
     }
   }
 
-  if (VAR == 0) {
+  if (VAR == 0 || VAR == 4) {
     if (active) {
       // t faces of a sub-lattice take their t-neighbours from the halos
       const int Vf = p.L[0] * p.L[1] * p.L[2];
@@ -853,7 +861,7 @@ __global__ void dslash_kernel(const DslashParams p) {
       hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[6], nb[6], x4, s0, Ls, b, c, mf);
       hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[7], nb[7], nb[7], s0, Ls, b, c, mf);
     }
-  } else if (VAR >= 2) {
+  } else if (VAR == 2 || VAR == 3) {
     if (PHI) {  // the (b + cK) input combination keeps the VAR 0 path
       if (active) {
         hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gauge, (C)lsg[0], nb[0], x4, s0, Ls, b, c, mf);
@@ -888,19 +896,46 @@ __global__ void dslash_kernel(const DslashParams p) {
       for (int j = 0; j < SPT; ++j) store(j, acc[j]);
     }
   } else if (OP == OP_D) {
-    // out = alpha psi + beta K psi - 1/2 Dhop phi
+    // out = alpha psi + beta K psi - 1/2 Dhop phi; optionally |out|^2 per CTA
+    // (the CG's <p, D^+D p> = |D p|^2, fused here to save a pass over two fields)
+    double nsq = 0.0;
     if (active) {
       roll_5d<P, false, SPT>(F, x4, s0, Ls, alpha, beta, mf, [&](int j, const Spinor<V2> &v) {
         Spinor<V2> o;
+        C ss = 0;
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
           o.up.re[cc] = p_fma(mhalf, acc[j].up.re[cc], v.up.re[cc]);
           o.up.im[cc] = p_fma(mhalf, acc[j].up.im[cc], v.up.im[cc]);
           o.lo.re[cc] = p_fma(mhalf, acc[j].lo.re[cc], v.lo.re[cc]);
           o.lo.im[cc] = p_fma(mhalf, acc[j].lo.im[cc], v.lo.im[cc]);
+          if (p.norm_partials) {
+            ss += o.up.re[cc].x * o.up.re[cc].x + o.up.re[cc].y * o.up.re[cc].y;
+            ss += o.up.im[cc].x * o.up.im[cc].x + o.up.im[cc].y * o.up.im[cc].y;
+            ss += o.lo.re[cc].x * o.lo.re[cc].x + o.lo.re[cc].y * o.lo.re[cc].y;
+            ss += o.lo.im[cc].x * o.lo.im[cc].x + o.lo.im[cc].y * o.lo.im[cc].y;
+          }
         }
+        nsq += (double)ss;
         store(j, o);
       });
+    }
+    if (p.norm_partials) {
+      // fixed-order block sum: warp shuffles, then warp 0 over the warp sums
+      __shared__ double warp_sums[32];
+      const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+      const int nwarps = (blockDim.x * blockDim.y + 31) / 32;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nsq += __shfl_down_sync(0xffffffffu, nsq, o);
+      if ((tid & 31) == 0) warp_sums[tid >> 5] = nsq;
+      __syncthreads();
+      if (tid < 32) {
+        double v = tid < nwarps ? warp_sums[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (tid == 0)
+          p.norm_partials[(long long)rhs * (gridDim.x / p.nrhs) + blockIdx.x / p.nrhs] = v;
+      }
     }
   } else {
     // OP_DDAG: out = alpha psi + beta K^+ psi - 1/2 (b + c K^+) Dhop^+ psi.
@@ -957,6 +992,26 @@ __global__ void dslash_kernel(const DslashParams p) {
 }
 
 template <class P, int OP, int SPT, int VAR>
+__global__ void dslash_kernel(const DslashParams p) {
+  dslash_body<P, OP, SPT, VAR>(p);
+}
+
+template <class P, int OP, int SPT, int VAR>
+__global__ void __launch_bounds__(LaunchBound<4>::threads, LaunchBound<4>::blocks)
+    dslash_kernel_capped(const DslashParams p) {
+  dslash_body<P, OP, SPT, VAR>(p);
+}
+
+// The kernel entry of (P, OP, SPT, VAR): variant 4 is the register-capped one.
+template <class P, int OP, int SPT, int VAR>
+constexpr void (*dslash_entry())(const DslashParams) {
+  if constexpr (VAR == 4)
+    return dslash_kernel_capped<P, OP, SPT, VAR>;
+  else
+    return dslash_kernel<P, OP, SPT, VAR>;
+}
+
+template <class P, int OP, int SPT, int VAR>
 size_t dslash_smem(int tx, int nchunk) {
   size_t smem = 0;
   if (VAR == 1) smem += kStages * StageLayout<P, OP == OP_D, SPT>::stage_bytes(tx * nchunk);
@@ -979,19 +1034,19 @@ int launch_one(const DslashParams &p, int tx, int zblk, cudaStream_t st) {
   static size_t smem_set = 48 * 1024;
   if (!max_threads) {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, SPT, VAR>) != cudaSuccess) return -1;
+    if (cudaFuncGetAttributes(&fa, dslash_entry<P, OP, SPT, VAR>()) != cudaSuccess) return -1;
     max_threads = fa.maxThreadsPerBlock;
   }
   if (tx < 32 || tx % 32 || tx * nchunk > max_threads) return -3;
   if (smem > 227 * 1024) return -3;
   if (smem > smem_set) {
-    if (cudaFuncSetAttribute(dslash_kernel<P, OP, SPT, VAR>,
+    if (cudaFuncSetAttribute(dslash_entry<P, OP, SPT, VAR>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return -3;
     smem_set = smem;
   }
-  dslash_kernel<P, OP, SPT, VAR><<<grid, block, smem, st>>>(q);
+  dslash_entry<P, OP, SPT, VAR>()<<<grid, block, smem, st>>>(q);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -1011,10 +1066,10 @@ int max_threads_var(int spt) {
   cudaFuncAttributes fa;
   cudaError_t e;
   switch (spt) {
-    case 1: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 1, VAR>); break;
-    case 2: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 2, VAR>); break;
-    case 3: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 3, VAR>); break;
-    case 4: e = cudaFuncGetAttributes(&fa, dslash_kernel<P, OP, 4, VAR>); break;
+    case 1: e = cudaFuncGetAttributes(&fa, dslash_entry<P, OP, 1, VAR>()); break;
+    case 2: e = cudaFuncGetAttributes(&fa, dslash_entry<P, OP, 2, VAR>()); break;
+    case 3: e = cudaFuncGetAttributes(&fa, dslash_entry<P, OP, 3, VAR>()); break;
+    case 4: e = cudaFuncGetAttributes(&fa, dslash_entry<P, OP, 4, VAR>()); break;
     default: return 0;
   }
   return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
