@@ -185,7 +185,8 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
  * direction; 1 = copied one direction ahead into shared memory with cp.async;
  * 2, 3 = loaded one (direction, slice) step ahead into registers, visiting
  * t,z,y,x (2) or x,y,z,t (3); 4 = variant 0 with registers capped for three
- * 192-thread CTAs per SM, FP32 only), and zblk, the number of z-blocks of the CTA
+ * 192-thread CTAs per SM, FP32 only; 5 = variant 0 with L2 eviction hints:
+ * t+ neighbours kept, t- neighbours evicted first; FP32 and FP16), and zblk, the number of z-blocks of the CTA
  * traversal order (planes are visited block by block, t inside a block; zblk
  * divides Lz; 0 in dw_set_tile = automatic).  A CTA holds all Ls/spt slice
  * groups of its tx sites.

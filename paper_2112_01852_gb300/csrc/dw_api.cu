@@ -366,7 +366,7 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d for Ls=%d Lz=%d (slices per thread "
-                "must divide Ls, tx a multiple of 32, variant 0..4, zblk dividing Lz, CTA within "
+                "must divide Ls, tx a multiple of 32, variant 0..5, zblk dividing Lz, CTA within "
                 "the kernel's limits)",
                 spt, tx, variant, zblk, lat->Ls, lat->dims[2]);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;

@@ -170,7 +170,7 @@ struct TileConfig {
   int variant;  // hop-phase load scheme, 0 .. kNumVariants-1 (see dw.h)
   int zblk;     // z-blocks of the CTA traversal order (divides Lz)
 };
-constexpr int kNumVariants = 5;
+constexpr int kNumVariants = 6;
 
 // Stencil launch at precision `prec`: 0 on success, -2 for a tile/variant
 // that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA

@@ -199,6 +199,67 @@ __device__ __forceinline__ void quad_in(double2 &re, double2 &im, const double2 
   re = __ldg(p);
   im = __ldg(p + plane);
 }
+// Loads with an L2 eviction-priority hint.  In the t-inside-a-z-block
+// traversal a spinor is first touched as a t+ neighbour and last touched as a
+// t- neighbour: the first touch is kept (evict_last) for the reuses that follow
+// one or two slabs later, the last touch may leave first (evict_first).
+enum { HINT_NONE = 0, HINT_KEEP = 1, HINT_DROP = 2 };
+template <int HINT>
+__device__ __forceinline__ unsigned long long l2_policy() {
+  unsigned long long pol = 0;
+  if (HINT == HINT_KEEP)
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else if (HINT == HINT_DROP)
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float4 ldg_hint(const float4 *p, unsigned long long pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint2 ldg_hint(const uint2 *p, unsigned long long pol) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ldg_hint(const double2 *p, unsigned long long pol) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y)
+               : "l"(p), "l"(pol));
+  return v;
+}
+template <int HINT, class VEC>
+__device__ __forceinline__ VEC ld_vec(const VEC *p, unsigned long long pol) {
+  if (HINT == HINT_NONE) return __ldg(p);
+  return ldg_hint(p, pol);
+}
+template <int HINT>
+__device__ __forceinline__ void quad_in_h(float2 &re, float2 &im, const float4 *p, long long,
+                                          unsigned long long pol) {
+  const float4 v = ld_vec<HINT>(p, pol);
+  re = make_float2(v.x, v.y);
+  im = make_float2(v.z, v.w);
+}
+template <int HINT>
+__device__ __forceinline__ void quad_in_h(float2 &re, float2 &im, const uint2 *p, long long,
+                                          unsigned long long pol) {
+  const uint2 v = ld_vec<HINT>(p, pol);
+  re = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+  im = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+}
+template <int HINT>
+__device__ __forceinline__ void quad_in_h(double2 &re, double2 &im, const double2 *p,
+                                          long long plane, unsigned long long pol) {
+  re = ld_vec<HINT>(p, pol);
+  im = ld_vec<HINT>(p + plane, pol);
+}
+
 // Outputs are written once and not re-read by the kernel: streaming stores
 // (evict-first) keep them from displacing neighbour spinors that are still to
 // be reused from L2.
@@ -234,6 +295,14 @@ struct Field {
     const vec *p = base + site(s, x4) + (long long)half * 3 * VPQ * plane;
 #pragma unroll
     for (int c = 0; c < 3; ++c) quad_in(h.re[c], h.im[c], p + (long long)c * VPQ * plane, plane);
+  }
+  template <int HINT>
+  __device__ __forceinline__ void load_half_h(Half<V2> &h, int x4, int s, int half,
+                                              unsigned long long pol) const {
+    const vec *p = base + site(s, x4) + (long long)half * 3 * VPQ * plane;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      quad_in_h<HINT>(h.re[c], h.im[c], p + (long long)c * VPQ * plane, plane, pol);
   }
 };
 
@@ -338,7 +407,7 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
 // One hop direction: acc[j] += (1 + S g_mu) W psi'(y4, s0 + j) for every j,
 // where W = U_mu(l4) (ADJ = false) or U_mu(l4)^+ (ADJ = true) and psi' is psi
 // itself (PHI = false) or phi = (b + cK) psi (PHI = true).
-template <class P, int MU, int S, bool ADJ, bool PHI, bool FIRST, int SPT>
+template <class P, int MU, int S, bool ADJ, bool PHI, bool FIRST, int SPT, int HINT = HINT_NONE>
 __device__ __forceinline__ void hop_dir(Spinor<typename Pair<P>::type> (&acc)[SPT],
                                         const Field<P> &F, const typename P::vec *gauge,
                                         typename P::C lsign, int y4, int l4, int s0, int Ls,
@@ -356,11 +425,12 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Pair<P>::type> (&acc)[SP
   if (PHI) {
     roll_5d<P, false, SPT>(F, y4, s0, Ls, b, c, mf, body);
   } else {
+    const unsigned long long pol = l2_policy<HINT>();
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
       Spinor<V2> v;
-      F.load_half(v.up, y4, s0 + j, 0);
-      F.load_half(v.lo, y4, s0 + j, 1);
+      F.template load_half_h<HINT>(v.up, y4, s0 + j, 0, pol);
+      F.template load_half_h<HINT>(v.lo, y4, s0 + j, 1, pol);
       body(j, v);
     }
   }
@@ -838,7 +908,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     }
   }
 
-  if (VAR == 0 || VAR == 4) {
+  if (VAR == 0 || VAR == 4 || VAR == 5) {
     if (active) {
       // t faces of a sub-lattice take their t-neighbours from the halos
       const int Vf = p.L[0] * p.L[1] * p.L[2];
@@ -849,11 +919,13 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         halo_hop_up<P, SF, true, SPT>(acc, (const vec *)p.halo_up + rhs * hrhs, hplane, Vf,
                                       x4 - ct * Vf, gauge, x4, (C)lsg[0], s0);
       else
-        hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gauge, (C)lsg[0], nb[0], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 3, SF, false, PHI, true, SPT, VAR == 5 ? HINT_KEEP : HINT_NONE>(
+            acc, F, gauge, (C)lsg[0], nb[0], x4, s0, Ls, b, c, mf);
       if (p.halo_dn && ct == 0)
         halo_hop_down<P, SB, SPT>(acc, (const vec *)p.halo_dn + rhs * hrhs, hplane, Vf, x4, s0);
       else
-        hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[1], nb[1], nb[1], s0, Ls, b, c, mf);
+        hop_dir<P, 3, SB, true, PHI, false, SPT, VAR == 5 ? HINT_DROP : HINT_NONE>(
+            acc, F, gauge, (C)lsg[1], nb[1], nb[1], s0, Ls, b, c, mf);
       hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[2], nb[2], x4, s0, Ls, b, c, mf);
       hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[3], nb[3], nb[3], s0, Ls, b, c, mf);
       hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[4], nb[4], x4, s0, Ls, b, c, mf);

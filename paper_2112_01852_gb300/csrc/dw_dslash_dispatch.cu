@@ -17,6 +17,8 @@ int launch_dslash_F32_v2(const DslashParams &p, int op, TileConfig cfg, cudaStre
 int dslash_max_threads_F32_v2(int op, int spt);
 int launch_dslash_F32_v3(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F32_v3(int op, int spt);
+int launch_dslash_F32_v5(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F32_v5(int op, int spt);
 int launch_dslash_F32_v4(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F32_v4(int op, int spt);
 int launch_dslash_F16_v0(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
@@ -27,6 +29,8 @@ int launch_dslash_F16_v2(const DslashParams &p, int op, TileConfig cfg, cudaStre
 int dslash_max_threads_F16_v2(int op, int spt);
 int launch_dslash_F16_v3(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v3(int op, int spt);
+int launch_dslash_F16_v5(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F16_v5(int op, int spt);
 
 int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st) {
   const int cfg_variant = cfg.variant;
@@ -43,6 +47,7 @@ int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaS
         case 1: return launch_dslash_F32_v1(p, op, cfg, st);
         case 2: return launch_dslash_F32_v2(p, op, cfg, st);
         case 3: return launch_dslash_F32_v3(p, op, cfg, st);
+        case 5: return launch_dslash_F32_v5(p, op, cfg, st);
         case 4: return launch_dslash_F32_v4(p, op, cfg, st);
         default: return -2;
       }
@@ -52,6 +57,7 @@ int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaS
         case 1: return launch_dslash_F16_v1(p, op, cfg, st);
         case 2: return launch_dslash_F16_v2(p, op, cfg, st);
         case 3: return launch_dslash_F16_v3(p, op, cfg, st);
+        case 5: return launch_dslash_F16_v5(p, op, cfg, st);
         default: return -2;
       }
   }
@@ -73,6 +79,7 @@ int dslash_max_threads(int prec, int op, int spt, int variant) {
         case 1: return dslash_max_threads_F32_v1(op, spt);
         case 2: return dslash_max_threads_F32_v2(op, spt);
         case 3: return dslash_max_threads_F32_v3(op, spt);
+        case 5: return dslash_max_threads_F32_v5(op, spt);
         case 4: return dslash_max_threads_F32_v4(op, spt);
         default: return 0;
       }
@@ -82,6 +89,7 @@ int dslash_max_threads(int prec, int op, int spt, int variant) {
         case 1: return dslash_max_threads_F16_v1(op, spt);
         case 2: return dslash_max_threads_F16_v2(op, spt);
         case 3: return dslash_max_threads_F16_v3(op, spt);
+        case 5: return dslash_max_threads_F16_v5(op, spt);
         default: return 0;
       }
   }

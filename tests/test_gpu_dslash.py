@@ -82,7 +82,7 @@ def test_all_tiles_ragged(Ls):
     lat.load_gauge(U)
     refs = {op: run_oracle(op, psi, U, dims, Ls, 1.6, 1.25, 0.75, mfs, bc) for op in STENCIL_OPS}
     ran = set()
-    for variant in range(4):
+    for variant in range(6):
         for spt, tx in valid_tiles(Ls):
             for op in STENCIL_OPS:
                 try:
@@ -121,7 +121,7 @@ def test_both_variants_low_precision(prec):
     lat.load_gauge(U)
     refs = {op: run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mfs) for op in STENCIL_OPS}
     ran = set()
-    for variant in range(4):
+    for variant in range(6):
         for spt in (1, 2, 3, 4):
             for op in STENCIL_OPS:
                 try:
@@ -131,7 +131,8 @@ def test_both_variants_low_precision(prec):
                 ran.add((variant, op))
                 got = run_gpu(lat, op, psi, mf=mfs)
                 assert max_rel(got, refs[op]) <= TOL[prec], (OP_NAMES[op], spt, variant)
-    assert {(v, op) for v in range(4) for op in STENCIL_OPS} <= ran
+    built = (0, 1, 2, 3, 4, 5) if prec == dw.DW_F32 else (0, 1, 2, 3, 5)
+    assert {(v, op) for v in built for op in STENCIL_OPS} <= ran
     lat.close()
 
 
@@ -230,7 +231,7 @@ def test_tune_picks_valid_tile_and_stays_exact():
         spt, tx, variant, zblk = lat.tune(op, 1)
         assert dims[2] % zblk == 0
         assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
-        assert variant in range(4)
+        assert variant in range(6)
         got = run_gpu(lat, op, psi, mf=[0.01])
         ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
         assert max_rel(got, ref) <= TOL[dw.DW_F32], OP_NAMES[op]
@@ -276,7 +277,7 @@ def test_argument_errors():
         lat.set_tile(dw.DW_OP_DHOP, 1, 48)  # not a multiple of 32
     assert e.value.code == dw.DW_ERR_ARG
     with pytest.raises(dw.DWError) as e:
-        lat.set_tile(dw.DW_OP_DHOP, 1, 32, variant=5)
+        lat.set_tile(dw.DW_OP_DHOP, 1, 32, variant=9)
     assert e.value.code == dw.DW_ERR_ARG
     with pytest.raises(dw.DWError) as e:
         lat.set_tile(dw.DW_OP_DHOP, 1, 32, zblk=3)  # 3 does not divide Lz = 4
