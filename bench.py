@@ -17,8 +17,10 @@ D^+D applies and the FP16-storage Dhop are timed too and reported under "ops".
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -45,6 +47,42 @@ def bytes_per_site(real_bytes: int, Ls: int, nrhs: int = 1) -> float:
     """Algorithmic HBM bytes per 5D site update: read psi once (24 reals), write
     once (24 reals), 4 links x 18 reals per 4D site shared by Ls*nrhs updates."""
     return real_bytes * (48 + 72.0 / (Ls * nrhs))
+
+
+# DRAM traffic of one Dhop launch, from a one-pass ncu capture of the full-size
+# workload (dram__bytes_read.sum + dram__bytes_write.sum).  The record names the
+# tile it was taken with and a digest of the stencil sources; when either no
+# longer matches, the traffic is reported as null.
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dslash_dhop_f32_32x32x32x64_ls12_dram.md")
+
+
+def kernel_digest() -> str:
+    """sha256 (first 16 hex digits) over the stencil kernel sources."""
+    csrc = os.path.join(ROOT, "paper_2112_01852_gb300", "csrc")
+    names = sorted(n for n in os.listdir(csrc)
+                   if n.startswith("dw_dslash") or n == "dw_common.cuh")
+    h = hashlib.sha256()
+    for n in names:
+        h.update(n.encode())
+        with open(os.path.join(csrc, n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(tile, dims, Ls):
+    """Bytes per launch from the traffic record if it applies to this kernel,
+    tile and workload, else None."""
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            kv = dict(m.groups() for m in re.finditer(r"^- (\w+): (.+?)\s*$", f.read(), re.M))
+        rec_tile = tuple(int(v) for v in kv["tile"].split(","))
+        rec_dims = tuple(int(v) for v in kv["dims"].split(","))
+        if (rec_tile != tuple(tile) or rec_dims != tuple(dims) or int(kv["Ls"]) != Ls
+                or kv["source_digest"] != kernel_digest()):
+            return None
+        return float(kv["dram_read_bytes"]) + float(kv["dram_write_bytes"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _peaks():
@@ -334,7 +372,7 @@ def main():
     ap.add_argument("--main-only", action="store_true",
                     help="time only the FP32 Dhop (no other operators, e2e, CG or CPU leg)")
     ap.add_argument("--tile", default=None,
-                    help="spt,tx[,variant[,zblk]]: fixed Dhop tile instead of tuning")
+                    help="spt,tx[,variant[,zblk[,sgrp]]]: fixed Dhop tile instead of tuning")
     ap.add_argument("--no-cg", action="store_true")
     args = ap.parse_args()
     global DIMS, LS
@@ -372,10 +410,10 @@ def main():
     y = lat.empty(1)
     tiles = {}
     if args.tile:
-        tv = [int(v) for v in args.tile.split(",")] + [0, 0]
-        spt, tx, var, zb = tv[0], tv[1], tv[2], tv[3]
-        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var, zblk=zb)
-        tiles[dw.DW_OP_DHOP] = (spt, tx, var, zb)
+        tv = [int(v) for v in args.tile.split(",")] + [0, 0, 1][len(args.tile.split(",")) - 2:]
+        spt, tx, var, zb, sg = tv[:5]
+        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var, zblk=zb, sgrp=sg)
+        tiles[dw.DW_OP_DHOP] = (spt, tx, var, zb, sg)
     else:
         tiles[dw.DW_OP_DHOP] = lat.tune(dw.DW_OP_DHOP, 1)
     if not args.main_only:
@@ -395,11 +433,13 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("dhop_timed")
     e0.record(stream)
     for _ in range(args.steps):
         dhop()
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     _barrier(ws)
     clocks = sampler.stop()
@@ -418,7 +458,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic", "config": _config(),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic(tiles[dw.DW_OP_DHOP], DIMS, LS),
                      "peak_source": peak_kind,
                      "bytes_per_site": bps, "sites_per_launch": V5},
         "gpu_launches": args.steps,
@@ -473,9 +514,11 @@ def main():
     lat.apply_host(dw.DW_OP_DHOP, hout, hin)
     e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("e2e_timed")
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         lat.apply_host(dw.DW_OP_DHOP, hout, hin)
+    torch.cuda.nvtx.range_pop()
     e2e_ms, e2e_rate = aggregate(ws, (time.perf_counter() - t0) / e2e_steps * 1e3, V5)
     e2e_s = e2e_ms * 1e-3
     e2e = {"value": FLOP_DHOP * e2e_rate / 1e9, "unit": "GFlop/s",

@@ -149,8 +149,15 @@ int dw_apply_DdagD_noalloc(dw_lattice *lat, void *out, const void *in, const dou
 /*
  * Apply operator `op` (DW_OP_*) with HOST buffers in the internal layout at
  * the lattice precision: copies in to the device, applies, copies out back and
- * synchronises the stream.  Device staging buffers are lattice-owned.
- * mf may be NULL for DW_OP_DHOP / DW_OP_DHOP_DAG.
+ * returns when the output is in out_host.  Device staging buffers are
+ * lattice-owned.  mf may be NULL for DW_OP_DHOP / DW_OP_DHOP_DAG.
+ * When Lx*Ly*Lz is a multiple of 32 the field moves in t slabs (up to 16, each
+ * of at least 8192 4D sites): the copy in of one slab, the operator on the
+ * previous one (once its t neighbours are resident) and the copy out of the
+ * one before run at the same time, on `stream` and two lattice-owned streams.
+ * Pinned host buffers (cudaHostAlloc / cudaHostRegister) are needed for the
+ * copies to overlap; pageable ones work but serialise.  out_host must not
+ * overlap in_host.
  */
 int dw_apply_host(dw_lattice *lat, int op, void *out_host, const void *in_host,
                   const double *mf, int nrhs, void *stream);
@@ -178,18 +185,21 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
                 double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
 
 /*
- * Stencil-kernel tiles.  A tile is (spt, tx, variant, zblk): spt fifth-dimension
+ * Stencil-kernel tiles.  A tile is (spt, tx, variant, zblk, sgrp): spt fifth-dimension
  * slices per thread (1..4, dividing Ls), tx 4D sites per CTA (a multiple of
  * 32, taken from one (x, y) plane), the load variant of the hop phase (0 =
  * neighbour spinors and links loaded straight into registers, direction by
  * direction; 1 = copied one direction ahead into shared memory with cp.async;
  * 2, 3 = loaded one (direction, slice) step ahead into registers, visiting
- * t,z,y,x (2) or x,y,z,t (3); 4 = variant 0 with registers capped for three
- * 192-thread CTAs per SM, FP32 only; 5 = variant 0 with L2 eviction hints:
- * t+ neighbours kept, t- neighbours evicted first; FP32 and FP16), and zblk, the number of z-blocks of the CTA
- * traversal order (planes are visited block by block, t inside a block; zblk
- * divides Lz; 0 in dw_set_tile = automatic).  A CTA holds all Ls/spt slice
- * groups of its tx sites.
+ * t,z,y,x (2) or x,y,z,t (3); 5 = variant 0 with L2 eviction hints: t+
+ * neighbours kept, t- neighbours evicted first; 4 = variant 5 with at most
+ * 128 registers per thread; FP64 builds 0 and 2 only), zblk, the
+ * number of z-blocks of the CTA traversal order (planes are visited block by
+ * block, t inside a block; zblk divides Lz; 0 in dw_set_tile = automatic), and
+ * sgrp, the number of CTAs that share one tile of tx sites: each holds
+ * Ls/(spt sgrp) slice groups (sgrp divides Ls/spt; DW_OP_DDAG needs sgrp = 1,
+ * its slice-group edges meet in shared memory).  Smaller CTAs let more of them
+ * fit on an SM when registers limit the occupancy.
  *
  * dw_set_tile pins the tile used for operator `op` (DW_OP_DHOP .. DW_OP_DDAG)
  * at precision `prec` for launches of `nrhs` right-hand sides (0 = any count
@@ -198,14 +208,14 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
  * dw_tune times every valid tile for (op, nrhs) at the lattice precision on
  * lattice-owned scratch fields (CUDA events on `stream`, median of a few
  * launches), keeps the fastest for later calls and returns it in *spt, *tx,
- * *variant, *zblk (any may be NULL).  Requires a loaded gauge field;
+ * *variant, *zblk, *sgrp (any may be NULL).  Requires a loaded gauge field;
  * synchronises; must not be called while `stream` is being captured into a
  * graph.
  */
 int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant,
-                int zblk);
+                int zblk, int sgrp);
 int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, int *zblk,
-            void *stream);
+            int *sgrp, void *stream);
 
 /*
  * Domain decomposition along t on one device ("virtual ranks").  The hopping

@@ -76,7 +76,7 @@ int auto_zblk(const dw_lattice *lat, int prec) {
 TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs) {
   (void)nrhs;
   const int Ls = lat->Ls;
-  TileConfig t{0, 32, 0, auto_zblk(lat, prec)};
+  TileConfig t{0, 32, 0, auto_zblk(lat, prec), 1};
   int maxt = 0;
   for (int spt : {1, 2, 3, 4}) {
     if (Ls % spt) continue;
@@ -109,7 +109,8 @@ bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (t.tx < 32 || t.tx % 32) return false;
   if (t.variant < 0 || t.variant > kNumVariants - 1) return false;
   if (t.zblk < 1 || lat->dims[2] % t.zblk) return false;
-  const long long threads = (long long)t.tx * (lat->Ls / t.spt);
+  if (t.sgrp < 1 || (lat->Ls / t.spt) % t.sgrp || (op == OP_DDAG && t.sgrp != 1)) return false;
+  const long long threads = (long long)t.tx * (lat->Ls / t.spt / t.sgrp);
   return threads <= 1024 && threads <= dslash_max_threads(prec, op, t.spt, t.variant);
 }
 
@@ -122,13 +123,13 @@ size_t halo_bytes(const dw_lattice *lat, int prec, int nrhs) {
 // CTAs per right-hand side of a stencil launch with tile `t`.
 long long dslash_ctas_per_rhs(const dw_lattice *lat, TileConfig t) {
   const long long per_plane = ((long long)lat->dims[0] * lat->dims[1] + t.tx - 1) / t.tx;
-  return per_plane * lat->dims[2] * lat->dims[3];
+  return per_plane * t.sgrp * lat->dims[2] * lat->dims[3];
 }
 
 int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
                const int *gate, int gate_stride, const void *halo_up, const void *halo_dn,
-               double *norm_partials) {
+               double *norm_partials, int t_begin, int t_count) {
   const size_t rhs_bytes = field_bytes(lat, prec, 1);
   const size_t hrhs_bytes = halo_bytes(lat, prec, 1);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
@@ -149,6 +150,8 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.gate_stride = gate_stride;
     p.halo_up = halo_up ? (const char *)halo_up + (size_t)r0 * hrhs_bytes : nullptr;
     p.halo_dn = halo_dn ? (const char *)halo_dn + (size_t)r0 * hrhs_bytes : nullptr;
+    p.t_begin = t_begin;
+    p.t_count = t_count;
     p.M5 = lat->M5;
     p.b = lat->b;
     p.c = lat->c;
@@ -273,6 +276,7 @@ void dw_destroy_lattice(dw_lattice *lat) {
   if (lat->stage_out) cudaFree(lat->stage_out);
   if (lat->partials) cudaFree(lat->partials);
   cg_release(lat);
+  pipe_release(lat);
   delete lat;
 }
 
@@ -336,45 +340,29 @@ int dw_apply_host(dw_lattice *lat, int op, void *out_host, const void *in_host, 
   if (need_mf && !mf) return fail(DW_ERR_ARG, "mf is NULL");
   if (nrhs < 1) return fail(DW_ERR_ARG, "nrhs must be >= 1");
   if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
-  const size_t bytes = field_bytes(lat, lat->prec, nrhs);
-  size_t cap_in = lat->stage_bytes, cap_out = lat->stage_bytes;
-  int rc = ensure_buffer(&lat->stage_in, &cap_in, bytes);
-  if (rc) return rc;
-  rc = ensure_buffer(&lat->stage_out, &cap_out, bytes);
-  if (rc) return rc;
-  lat->stage_bytes = cap_in < cap_out ? cap_in : cap_out;
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(lat->stage_in, in_host, bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-  rc = apply_op(lat, op, lat->stage_out, lat->stage_in, mf, nrhs, st);
-  if (rc) return rc;
-  e = cudaMemcpyAsync(out_host, lat->stage_out, bytes, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
-  return DW_OK;
+  return apply_host_pipelined(lat, op, out_host, in_host, mf, nrhs, (cudaStream_t)stream);
 }
 
 int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, int variant,
-                int zblk) {
+                int zblk, int sgrp) {
   clear_error();
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
   if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
   if (prec < DW_F64 || prec > DW_F16) return fail(DW_ERR_ARG, "unknown precision %d", prec);
   if (nrhs < 0) return fail(DW_ERR_ARG, "nrhs must be >= 0");
-  TileConfig t{spt, tx, variant, zblk == 0 ? auto_zblk(lat, prec) : zblk};
+  TileConfig t{spt, tx, variant, zblk == 0 ? auto_zblk(lat, prec) : zblk, sgrp};
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
-                "invalid tile spt=%d tx=%d variant=%d zblk=%d for Ls=%d Lz=%d (slices per thread "
-                "must divide Ls, tx a multiple of 32, variant 0..5, zblk dividing Lz, CTA within "
-                "the kernel's limits)",
-                spt, tx, variant, zblk, lat->Ls, lat->dims[2]);
+                "invalid tile spt=%d tx=%d variant=%d zblk=%d sgrp=%d for Ls=%d Lz=%d (slices "
+                "per thread must divide Ls, tx a multiple of 32, variant 0..5, zblk dividing Lz, "
+                "sgrp dividing Ls/spt and 1 for D^+, CTA within the kernel's limits)",
+                spt, tx, variant, zblk, sgrp, lat->Ls, lat->dims[2]);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;
   return DW_OK;
 }
 
 int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, int *zblk,
-            void *stream) {
+            int *sgrp, void *stream) {
   clear_error();
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
   if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
@@ -391,6 +379,7 @@ int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, 
   if (tx) *tx = t.tx;
   if (variant) *variant = t.variant;
   if (zblk) *zblk = t.zblk;
+  if (sgrp) *sgrp = t.sgrp;
   return DW_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <map>
+#include <vector>
 #include <string>
 #include <tuple>
 
@@ -157,6 +158,9 @@ struct DslashParams {
   const void *halo_dn;  // optional t-face halves from the rank below (variant 0 only)
   int tiles_per_plane;  // set by the launcher: CTAs per (x, y) plane
   int zblk;             // set by the launcher: z-blocks of the traversal order
+  int sgrp;             // set by the launcher: CTAs per site tile (slice groups)
+  int t_begin;          // output sites: the time slices t_begin .. t_begin + t_count - 1
+  int t_count;          // (0: all Lt; the inputs are read on the whole lattice)
   double M5, b, c;
   double mf[64];         // per-RHS masses, passed by value
 };
@@ -169,6 +173,7 @@ struct TileConfig {
   int tx;       // 4D sites per CTA (multiple of 32)
   int variant;  // hop-phase load scheme, 0 .. kNumVariants-1 (see dw.h)
   int zblk;     // z-blocks of the CTA traversal order (divides Lz)
+  int sgrp;     // CTAs sharing one tile of sites, each with Ls / (spt sgrp) thread rows
 };
 constexpr int kNumVariants = 6;
 
@@ -212,6 +217,9 @@ struct dw_lattice {
   size_t scratch_bytes;
   void *stage_in, *stage_out;
   size_t stage_bytes;
+  // host-buffer apply: copy-in and copy-out streams and their events
+  cudaStream_t pipe_in, pipe_out;
+  std::vector<cudaEvent_t> pipe_events;
   double *partials;   // reduction partials
   size_t partials_cap;
   // tuning cache: (prec, op, nrhs) -> tile

@@ -809,12 +809,54 @@ int launch_halo_pack_impl(const DslashParams &p, void *send_dn, void *send_up, i
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Variant 4 is variant 0 compiled for at most 192 threads per CTA and three
-// resident CTAs per SM (a register cap that trades spills for occupancy).
+// Neighbour addressing that keeps one word per thread instead of eight
+// neighbour indices and eight link signs: bit 2 mu of `edge` says the site is
+// on the upper face in direction mu (c_mu = L_mu - 1), bit 2 mu + 1 that it is
+// on the lower face (c_mu = 0).  Indices and signs are rebuilt per hop from
+// the launch parameters.
+struct Hops {
+  int x4;
+  unsigned edge;
+  __device__ __forceinline__ Hops(const DslashParams &p, int x4_) : x4(x4_), edge(0u) {
+    int rem = x4_;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int c = (m < 3) ? rem % p.L[m] : rem;
+      rem /= p.L[m];
+      edge |= (unsigned)(c == p.L[m] - 1) << (2 * m);
+      edge |= (unsigned)(c == 0) << (2 * m + 1);
+    }
+  }
+  template <int MU>
+  __device__ __forceinline__ static int stride(const DslashParams &p) {
+    int st = 1;
+#pragma unroll
+    for (int m = 0; m < MU; ++m) st *= p.L[m];
+    return st;
+  }
+  // x4 + mu (FWD) or x4 - mu, periodic
+  template <int MU, bool FWD>
+  __device__ __forceinline__ int nb(const DslashParams &p) const {
+    const int st = stride<MU>(p);
+    const bool at = (edge >> (2 * MU + (FWD ? 0 : 1))) & 1u;
+    if (FWD) return at ? x4 - (p.L[MU] - 1) * st : x4 + st;
+    return at ? x4 + (p.L[MU] - 1) * st : x4 - st;
+  }
+  // boundary sign of the link the hop uses
+  template <int MU, bool FWD>
+  __device__ __forceinline__ int sign(const DslashParams &p) const {
+    return ((edge >> (2 * MU + (FWD ? 0 : 1))) & 1u) ? p.bc[MU] : 1;
+  }
+};
+
+// Variant 4 is variant 5 compiled with at most 128 registers per thread.  The
+// kernel is latency bound: with CTAs of one or two warps (sgrp > 1) 16 warps
+// fit on an SM instead of 12 at the uncapped ~140 registers, and the extra
+// loads in flight outweigh a few spilled registers.  (Caps of 112 and 96
+// registers spill more and ran slower at 32^3 x 64 x 12.)
 template <int VAR>
-struct LaunchBound {
-  static constexpr int threads = VAR == 4 ? 192 : 1024;
-  static constexpr int blocks = VAR == 4 ? 3 : 1;
+struct RegCap {
+  static constexpr int value = VAR == 4 ? 128 : 0;
 };
 
 template <class P, int OP, int SPT, int VAR>
@@ -835,21 +877,23 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   // planes instead of 2 Lz: the L2 then holds the reuse window.
   const int tx = blockDim.x;
   const int rhs = blockIdx.x % p.nrhs;
-  int x4, in_plane;
+  int x4, in_plane, sg;
   {
     int id = blockIdx.x / p.nrhs;
+    sg = id % p.sgrp;  // slice group: the CTAs of one tile are adjacent
+    id /= p.sgrp;
     const int tile = id % p.tiles_per_plane;
     id /= p.tiles_per_plane;
     const int bz = p.L[2] / p.zblk;
     const int zl = id % bz;
     id /= bz;
-    const int t = id % p.L[3];
-    const int zb = id / p.L[3];
+    const int t = p.t_begin + id % p.t_count;
+    const int zb = id / p.t_count;
     in_plane = tile * tx + threadIdx.x;
     x4 = in_plane + p.L[0] * p.L[1] * ((zb * bz + zl) + p.L[2] * t);
   }
-  const int chunk = threadIdx.y;
-  const int nchunk = blockDim.y;
+  const int chunk = threadIdx.y + sg * blockDim.y;  // slice group of this thread row
+  const int nchunk = blockDim.y;                     // thread rows of the CTA
   if (p.gate && !p.gate[(long long)rhs * p.gate_stride]) return;  // whole CTA: uniform
   const bool active = in_plane < p.L[0] * p.L[1];
   const int s0 = chunk * SPT;
@@ -873,7 +917,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
 
   int nb[8];   // neighbours in the order t+, t-, z+, z-, y+, y-, x+, x-
   int lsg[8];  // boundary sign of the link each of those hops uses
-  if (active) {
+  // (variants 0, 4, 5 rebuild both per hop from the edge flags of Hops)
+  if (active && (VAR == 1 || VAR == 2 || VAR == 3)) {
     int rem = x4;
     const int cx = rem % p.L[0];
     rem /= p.L[0];
@@ -908,8 +953,9 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     }
   }
 
-  if (VAR == 0 || VAR == 4 || VAR == 5) {
+  if (VAR == 0 || VAR >= 4) {
     if (active) {
+      const Hops H(p, x4);
       // t faces of a sub-lattice take their t-neighbours from the halos
       const int Vf = p.L[0] * p.L[1] * p.L[2];
       const int ct = x4 / Vf;
@@ -917,21 +963,27 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       const long long hrhs = hplane * (12 / P::R);
       if (p.halo_up && ct == p.L[3] - 1)
         halo_hop_up<P, SF, true, SPT>(acc, (const vec *)p.halo_up + rhs * hrhs, hplane, Vf,
-                                      x4 - ct * Vf, gauge, x4, (C)lsg[0], s0);
+                                      x4 - ct * Vf, gauge, x4, (C)H.sign<3, true>(p), s0);
       else
-        hop_dir<P, 3, SF, false, PHI, true, SPT, VAR == 5 ? HINT_KEEP : HINT_NONE>(
-            acc, F, gauge, (C)lsg[0], nb[0], x4, s0, Ls, b, c, mf);
+        hop_dir<P, 3, SF, false, PHI, true, SPT, VAR >= 4 ? HINT_KEEP : HINT_NONE>(
+            acc, F, gauge, (C)H.sign<3, true>(p), H.nb<3, true>(p), x4, s0, Ls, b, c, mf);
       if (p.halo_dn && ct == 0)
         halo_hop_down<P, SB, SPT>(acc, (const vec *)p.halo_dn + rhs * hrhs, hplane, Vf, x4, s0);
       else
-        hop_dir<P, 3, SB, true, PHI, false, SPT, VAR == 5 ? HINT_DROP : HINT_NONE>(
-            acc, F, gauge, (C)lsg[1], nb[1], nb[1], s0, Ls, b, c, mf);
-      hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[2], nb[2], x4, s0, Ls, b, c, mf);
-      hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[3], nb[3], nb[3], s0, Ls, b, c, mf);
-      hop_dir<P, 1, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[4], nb[4], x4, s0, Ls, b, c, mf);
-      hop_dir<P, 1, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[5], nb[5], nb[5], s0, Ls, b, c, mf);
-      hop_dir<P, 0, SF, false, PHI, false, SPT>(acc, F, gauge, (C)lsg[6], nb[6], x4, s0, Ls, b, c, mf);
-      hop_dir<P, 0, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[7], nb[7], nb[7], s0, Ls, b, c, mf);
+        hop_dir<P, 3, SB, true, PHI, false, SPT, VAR >= 4 ? HINT_DROP : HINT_NONE>(
+            acc, F, gauge, (C)H.sign<3, false>(p), H.nb<3, false>(p), H.nb<3, false>(p), s0, Ls,
+            b, c, mf);
+#define DW_HOP(MU, FWD, S, ADJ)                                                                  \
+  hop_dir<P, MU, S, ADJ, PHI, false, SPT>(acc, F, gauge, (C)H.sign<MU, FWD>(p),                \
+                                          H.nb<MU, FWD>(p), FWD ? x4 : H.nb<MU, FWD>(p), s0,    \
+                                          Ls, b, c, mf)
+      DW_HOP(2, true, SF, false);
+      DW_HOP(2, false, SB, true);
+      DW_HOP(1, true, SF, false);
+      DW_HOP(1, false, SB, true);
+      DW_HOP(0, true, SF, false);
+      DW_HOP(0, false, SB, true);
+#undef DW_HOP
     }
   } else if (VAR == 2 || VAR == 3) {
     if (PHI) {  // the (b + cK) input combination keeps the VAR 0 path
@@ -952,7 +1004,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     StagedHop<P, OP, SPT> H;
     H.smem = smem_raw;
     H.T = tx * nchunk;
-    H.t = chunk * tx + threadIdx.x;
+    H.t = threadIdx.y * tx + threadIdx.x;
     hop_staged<P, OP, SPT>(acc, H, F, gauge, x4, active, nb, lsg, s0, Ls, b, c, mf);
     smem_used = kStages * StageLayout<P, PHI, SPT>::stage_bytes(H.T);
   }
@@ -1069,15 +1121,14 @@ __global__ void dslash_kernel(const DslashParams p) {
 }
 
 template <class P, int OP, int SPT, int VAR>
-__global__ void __launch_bounds__(LaunchBound<4>::threads, LaunchBound<4>::blocks)
-    dslash_kernel_capped(const DslashParams p) {
+__global__ void __maxnreg__(RegCap<VAR>::value) dslash_kernel_capped(const DslashParams p) {
   dslash_body<P, OP, SPT, VAR>(p);
 }
 
-// The kernel entry of (P, OP, SPT, VAR): variant 4 is the register-capped one.
+// The kernel entry of (P, OP, SPT, VAR): variant 4 is register capped.
 template <class P, int OP, int SPT, int VAR>
 constexpr void (*dslash_entry())(const DslashParams) {
-  if constexpr (VAR == 4)
+  if constexpr (RegCap<VAR>::value > 0)
     return dslash_kernel_capped<P, OP, SPT, VAR>;
   else
     return dslash_kernel<P, OP, SPT, VAR>;
@@ -1092,14 +1143,22 @@ size_t dslash_smem(int tx, int nchunk) {
 }
 
 template <class P, int OP, int SPT, int VAR>
-int launch_one(const DslashParams &p, int tx, int zblk, cudaStream_t st) {
-  const int nchunk = p.Ls / SPT;
+int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t st) {
+  // D^+ exchanges slice-group edges through shared memory: one CTA per tile
+  if (sgrp < 1 || (p.Ls / SPT) % sgrp || (OP == OP_DDAG && sgrp != 1)) return -2;
+  const int nchunk = p.Ls / SPT / sgrp;
   dim3 block(tx, nchunk);
   DslashParams q = p;
   q.tiles_per_plane = (p.L[0] * p.L[1] + tx - 1) / tx;
   q.zblk = zblk;
+  q.sgrp = sgrp;
   if (zblk < 1 || p.L[2] % zblk) return -2;
-  dim3 grid((unsigned)((long long)q.tiles_per_plane * p.L[2] * p.L[3] * p.nrhs));
+  if (q.t_count == 0) {
+    q.t_begin = 0;
+    q.t_count = p.L[3];
+  }
+  if (q.t_begin < 0 || q.t_count < 1 || q.t_begin + q.t_count > p.L[3]) return -2;
+  dim3 grid((unsigned)((long long)q.tiles_per_plane * sgrp * p.L[2] * q.t_count * p.nrhs));
   const size_t smem = dslash_smem<P, OP, SPT, VAR>(tx, nchunk);
   // per-instantiation launch limits, queried once
   static int max_threads = 0;
@@ -1125,10 +1184,10 @@ int launch_one(const DslashParams &p, int tx, int zblk, cudaStream_t st) {
 template <class P, int OP, int VAR>
 int launch_spt(const DslashParams &p, TileConfig cfg, cudaStream_t st) {
   switch (cfg.spt) {
-    case 1: return launch_one<P, OP, 1, VAR>(p, cfg.tx, cfg.zblk, st);
-    case 2: return launch_one<P, OP, 2, VAR>(p, cfg.tx, cfg.zblk, st);
-    case 3: return launch_one<P, OP, 3, VAR>(p, cfg.tx, cfg.zblk, st);
-    case 4: return launch_one<P, OP, 4, VAR>(p, cfg.tx, cfg.zblk, st);
+    case 1: return launch_one<P, OP, 1, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
+    case 2: return launch_one<P, OP, 2, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
+    case 3: return launch_one<P, OP, 3, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
+    case 4: return launch_one<P, OP, 4, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
     default: return -2;
   }
 }

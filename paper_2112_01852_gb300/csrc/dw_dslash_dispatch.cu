@@ -17,10 +17,10 @@ int launch_dslash_F32_v2(const DslashParams &p, int op, TileConfig cfg, cudaStre
 int dslash_max_threads_F32_v2(int op, int spt);
 int launch_dslash_F32_v3(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F32_v3(int op, int spt);
-int launch_dslash_F32_v5(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
-int dslash_max_threads_F32_v5(int op, int spt);
 int launch_dslash_F32_v4(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F32_v4(int op, int spt);
+int launch_dslash_F32_v5(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F32_v5(int op, int spt);
 int launch_dslash_F16_v0(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v0(int op, int spt);
 int launch_dslash_F16_v1(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
@@ -29,6 +29,8 @@ int launch_dslash_F16_v2(const DslashParams &p, int op, TileConfig cfg, cudaStre
 int dslash_max_threads_F16_v2(int op, int spt);
 int launch_dslash_F16_v3(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v3(int op, int spt);
+int launch_dslash_F16_v4(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F16_v4(int op, int spt);
 int launch_dslash_F16_v5(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v5(int op, int spt);
 
@@ -47,8 +49,8 @@ int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaS
         case 1: return launch_dslash_F32_v1(p, op, cfg, st);
         case 2: return launch_dslash_F32_v2(p, op, cfg, st);
         case 3: return launch_dslash_F32_v3(p, op, cfg, st);
-        case 5: return launch_dslash_F32_v5(p, op, cfg, st);
         case 4: return launch_dslash_F32_v4(p, op, cfg, st);
+        case 5: return launch_dslash_F32_v5(p, op, cfg, st);
         default: return -2;
       }
     case DW_F16:
@@ -57,6 +59,7 @@ int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaS
         case 1: return launch_dslash_F16_v1(p, op, cfg, st);
         case 2: return launch_dslash_F16_v2(p, op, cfg, st);
         case 3: return launch_dslash_F16_v3(p, op, cfg, st);
+        case 4: return launch_dslash_F16_v4(p, op, cfg, st);
         case 5: return launch_dslash_F16_v5(p, op, cfg, st);
         default: return -2;
       }
@@ -79,8 +82,8 @@ int dslash_max_threads(int prec, int op, int spt, int variant) {
         case 1: return dslash_max_threads_F32_v1(op, spt);
         case 2: return dslash_max_threads_F32_v2(op, spt);
         case 3: return dslash_max_threads_F32_v3(op, spt);
-        case 5: return dslash_max_threads_F32_v5(op, spt);
         case 4: return dslash_max_threads_F32_v4(op, spt);
+        case 5: return dslash_max_threads_F32_v5(op, spt);
         default: return 0;
       }
     case DW_F16:
@@ -89,6 +92,7 @@ int dslash_max_threads(int prec, int op, int spt, int variant) {
         case 1: return dslash_max_threads_F16_v1(op, spt);
         case 2: return dslash_max_threads_F16_v2(op, spt);
         case 3: return dslash_max_threads_F16_v3(op, spt);
+        case 4: return dslash_max_threads_F16_v4(op, spt);
         case 5: return dslash_max_threads_F16_v5(op, spt);
         default: return 0;
       }

@@ -1,4 +1,4 @@
-// F32 storage, hop-phase variant 4 (variant 0 under a 3-CTA register cap).
+// F32 storage, hop-phase variant 4 (variant 5 with at most 128 registers per thread).
 #include "dw_dslash.cuh"
 
 DW_DSLASH_INSTANTIATE(F32, 4)

@@ -28,33 +28,35 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
   for (int variant = 0; variant < kNumVariants; ++variant)
     for (int spt : {1, 2, 3, 4})
       for (int tx : {32, 64, 128, 256})
-        for (int zblk : {1, 2, 4}) {
-          TileConfig t{spt, tx, variant, zblk};
-          if (zblk != 1 && zblk != za) continue;  // unblocked and the automatic blocking
-          if (quick && (tx > 64 || zblk != za)) continue;
-          if (!tile_valid(lat, prec, op, t)) continue;
-          // warm-up launch doubles as the validity check
-          if (run_dslash(lat, prec, op, lat->stage_out, lat->stage_in, mf.data(), nrhs, st, &t)) {
-            cudaGetLastError();
-            continue;
+        for (int zblk : {1, 2, 4})
+          for (int sgrp : {1, 2, 3, 4, 6}) {
+            TileConfig t{spt, tx, variant, zblk, sgrp};
+            if (zblk != 1 && zblk != za) continue;  // unblocked and the automatic blocking
+            if (sgrp > 1 && tx > 32) continue;      // split only the narrowest CTAs
+            if (quick && (tx > 64 || zblk != za || sgrp > 2)) continue;
+            if (!tile_valid(lat, prec, op, t)) continue;
+            // warm-up launch doubles as the validity check
+            if (run_dslash(lat, prec, op, lat->stage_out, lat->stage_in, mf.data(), nrhs, st, &t)) {
+              cudaGetLastError();
+              continue;
+            }
+            std::vector<float> ms;
+            for (int r = 0; r < reps; ++r) {
+              cudaEventRecord(e0, st);
+              run_dslash(lat, prec, op, lat->stage_out, lat->stage_in, mf.data(), nrhs, st, &t);
+              cudaEventRecord(e1, st);
+              cudaEventSynchronize(e1);
+              float m = 0.f;
+              cudaEventElapsedTime(&m, e0, e1);
+              ms.push_back(m);
+            }
+            std::sort(ms.begin(), ms.end());
+            const float med = ms[ms.size() / 2];
+            if (med < best) {
+              best = med;
+              best_t = t;
+            }
           }
-          std::vector<float> ms;
-          for (int r = 0; r < reps; ++r) {
-            cudaEventRecord(e0, st);
-            run_dslash(lat, prec, op, lat->stage_out, lat->stage_in, mf.data(), nrhs, st, &t);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float m = 0.f;
-            cudaEventElapsedTime(&m, e0, e1);
-            ms.push_back(m);
-          }
-          std::sort(ms.begin(), ms.end());
-          const float med = ms[ms.size() / 2];
-          if (med < best) {
-            best = med;
-            best_t = t;
-          }
-        }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   clear_error();

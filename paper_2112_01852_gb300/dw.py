@@ -104,8 +104,8 @@ def load_library():
             "dw_apply_DdagD_noalloc": (I, [P, P, P, DP, I, P]),
             "dw_apply_host": (I, [P, I, P, P, DP, I, P]),
             "dw_cg_solve": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
-            "dw_set_tile": (I, [P, I, I, I, I, I, I, I]),
-            "dw_tune": (I, [P, I, I, IP, IP, IP, IP, P]),
+            "dw_set_tile": (I, [P, I, I, I, I, I, I, I, I]),
+            "dw_tune": (I, [P, I, I, IP, IP, IP, IP, IP, P]),
             "dw_halo_bytes": (S, [P, I, I]),
             "dw_halo_pack": (I, [P, P, P, P, I, I, P]),
             "dw_apply_Dhop_halo": (I, [P, P, P, P, P, I, I, P]),
@@ -201,14 +201,14 @@ def dw_cg_solve(lat, x, b, mf, nrhs, tol, maxit, mode, stream=0):
     return rc, list(stats)
 
 
-def dw_set_tile(lat, op, prec, nrhs, spt, tx, variant=0, zblk=0):
+def dw_set_tile(lat, op, prec, nrhs, spt, tx, variant=0, zblk=0, sgrp=1):
     _check(load_library().dw_set_tile(lat, int(op), int(prec), int(nrhs), int(spt), int(tx),
-                                      int(variant), int(zblk)))
+                                      int(variant), int(zblk), int(sgrp)))
 
 
 def dw_tune(lat, op, nrhs, stream=0):
-    """Returns the chosen (spt, tx, variant, zblk)."""
-    vals = [ctypes.c_int() for _ in range(4)]
+    """Returns the chosen (spt, tx, variant, zblk, sgrp)."""
+    vals = [ctypes.c_int() for _ in range(5)]
     _check(load_library().dw_tune(lat, int(op), int(nrhs), *[ctypes.byref(v) for v in vals],
                                   stream))
     return tuple(v.value for v in vals)

@@ -109,9 +109,9 @@ class Lattice:
         dw.dw_apply_host(self.handle, op, out_host.data_ptr(), in_host.data_ptr(),
                          None if mf is None else _masses(mf, nrhs), nrhs, _stream())
 
-    def set_tile(self, op, spt, tx, variant=0, nrhs=0, prec=None, zblk=0):
+    def set_tile(self, op, spt, tx, variant=0, nrhs=0, prec=None, zblk=0, sgrp=1):
         dw.dw_set_tile(self.handle, op, self.prec if prec is None else prec, nrhs, spt, tx,
-                       variant, zblk)
+                       variant, zblk, sgrp)
 
     def tune(self, op, nrhs=1):
         return dw.dw_tune(self.handle, op, nrhs, _stream())

@@ -99,6 +99,35 @@ def test_all_tiles_ragged(Ls):
     lat.close()
 
 
+@pytest.mark.parametrize("prec", [dw.DW_F64, dw.DW_F32, dw.DW_F16], ids=["f64", "f32", "f16"])
+def test_slice_groups_equal_one_cta(prec):
+    # splitting the slices of a tile over sgrp CTAs changes only which CTA
+    # computes a site: the result is the same bit for bit
+    dims, Ls = (8, 4, 6, 10), 12
+    U, psi = make_case(dims, Ls, 2, seed=16)
+    mfs = [0.01, 0.04]
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
+    lat.load_gauge(U)
+    ran = 0
+    for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG, dw.DW_OP_D):
+        for variant in range(6):
+            for spt in (1, 2, 3):
+                try:
+                    lat.set_tile(op, spt, 32, variant)
+                except dw.DWError:
+                    continue
+                ref = run_gpu(lat, op, psi, mf=mfs)
+                for sgrp in (2, 3, 4, 6, 12):
+                    if (Ls // spt) % sgrp:
+                        continue
+                    lat.set_tile(op, spt, 32, variant, sgrp=sgrp)
+                    got = run_gpu(lat, op, psi, mf=mfs)
+                    assert np.array_equal(got, ref), (OP_NAMES[op], variant, spt, sgrp)
+                    ran += 1
+    assert ran > 0
+    lat.close()
+
+
 def test_two_site_lattice_sums_coinciding_neighbours():
     # On a 2^4 lattice x+mu and x-mu are the same site: both hops must add.
     dims, Ls = (2, 2, 2, 2), 4
@@ -131,7 +160,7 @@ def test_both_variants_low_precision(prec):
                 ran.add((variant, op))
                 got = run_gpu(lat, op, psi, mf=mfs)
                 assert max_rel(got, refs[op]) <= TOL[prec], (OP_NAMES[op], spt, variant)
-    built = (0, 1, 2, 3, 4, 5) if prec == dw.DW_F32 else (0, 1, 2, 3, 5)
+    built = tuple(range(6))
     assert {(v, op) for v in built for op in STENCIL_OPS} <= ran
     lat.close()
 
@@ -222,15 +251,38 @@ def test_apply_host_matches_device():
     lat.close()
 
 
+@pytest.mark.parametrize("dims", [(16, 16, 8, 16), (32, 16, 16, 16), (16, 16, 16, 6)],
+                         ids=["4slabs", "16slabs_T1", "3slabs"])
+def test_apply_host_slab_pipeline_matches_device(dims):
+    # Lx Ly Lz a multiple of 32: the host apply moves the field in t slabs
+    # (4, 16 of one time slice, 3) and must equal the device apply bit for bit
+    import torch
+    Ls = 4
+    U, psi = make_case(dims, Ls, 2, seed=14)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
+    lat.load_gauge(U)
+    x = lat.pack(psi)
+    hin = x.cpu().pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for op in ALL_OPS:
+        dev = run_gpu(lat, op, psi, mf=[0.01, 0.02])
+        hout.zero_()
+        lat.apply_host(op, hout, hin, mf=None if op < dw.DW_OP_D else [0.01, 0.02], nrhs=2)
+        host = lat.unpack(hout.cuda(), 2)
+        assert np.array_equal(host, dev), OP_NAMES[op]
+    lat.close()
+
+
 def test_tune_picks_valid_tile_and_stays_exact():
     dims, Ls = (8, 8, 8, 8), 12
     U, psi = make_case(dims, Ls, 1, seed=13)
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
     lat.load_gauge(U)
     for op in STENCIL_OPS:
-        spt, tx, variant, zblk = lat.tune(op, 1)
+        spt, tx, variant, zblk, sgrp = lat.tune(op, 1)
         assert dims[2] % zblk == 0
         assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
+        assert (Ls // spt) % sgrp == 0 and (sgrp == 1 or op != dw.DW_OP_DDAG)
         assert variant in range(6)
         got = run_gpu(lat, op, psi, mf=[0.01])
         ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
@@ -281,6 +333,12 @@ def test_argument_errors():
     assert e.value.code == dw.DW_ERR_ARG
     with pytest.raises(dw.DWError) as e:
         lat.set_tile(dw.DW_OP_DHOP, 1, 32, zblk=3)  # 3 does not divide Lz = 4
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        lat.set_tile(dw.DW_OP_DHOP, 1, 32, sgrp=3)  # 3 does not divide Ls / spt = 4
+    assert e.value.code == dw.DW_ERR_ARG
+    with pytest.raises(dw.DWError) as e:
+        lat.set_tile(dw.DW_OP_DDAG, 1, 32, sgrp=2)  # D^+ keeps all slices in one CTA
     assert e.value.code == dw.DW_ERR_ARG
     assert "multiple" in dw.dw_last_error() or "invalid" in dw.dw_last_error()
     torch.cuda.synchronize()
