@@ -193,7 +193,10 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
  * 2, 3 = loaded one (direction, slice) step ahead into registers, visiting
  * t,z,y,x (2) or x,y,z,t (3); 5 = variant 0 with L2 eviction hints: t+
  * neighbours kept, t- neighbours evicted first; 4 = variant 5 with at most
- * 128 registers per thread; FP64 builds 0 and 2 only), zblk, the
+ * 128 registers per thread; 6 = variant 4 with the tile's x rows and their two
+ * y-neighbour rows bulk-copied into shared memory, the x and y hops read there
+ * (needs Lx = 32, tx dividing Lx*Ly, DW_OP_DHOP / DW_OP_DHOP_DAG only; its
+ * bounded wait reports through dw_device_status); FP64 builds 0 and 2 only), zblk, the
  * number of z-blocks of the CTA traversal order (planes are visited block by
  * block, t inside a block; zblk divides Lz; 0 in dw_set_tile = automatic), and
  * sgrp, the number of CTAs that share one tile of tx sites: each holds
@@ -216,6 +219,15 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
                 int zblk, int sgrp);
 int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, int *zblk,
             int *sgrp, void *stream);
+
+/*
+ * Device-side status of the lattice's kernels.  Kernels that wait for their own
+ * asynchronous copies (stencil variant 6) bound every wait; one that gives up
+ * sets a lattice-owned device word and returns without finishing (its output is
+ * then wrong).  This call synchronises the device, reads and clears the word and
+ * returns DW_OK or DW_ERR_TIMEOUT.
+ */
+int dw_device_status(dw_lattice *lat);
 
 /*
  * Domain decomposition along t on one device ("virtual ranks").  The hopping

@@ -61,12 +61,13 @@ int ensure_buffer(void **buf, size_t *cap, size_t need) {
 }
 
 // z-blocks of the traversal order: the fewest that keep the t-reuse window of
-// the input (2 * Lz/zblk planes x Ls slices) within ~40 MB of L2.
+// the input (2 * Lz/zblk planes x Ls slices) within ~20 MB of L2 (measured best
+// at 32^3 x 64 x 12: 4 z-blocks; 2 and 8 were slower).
 int auto_zblk(const dw_lattice *lat, int prec) {
   const double plane = (double)lat->dims[0] * lat->dims[1] * lat->Ls * 24.0 * prec_real_bytes(prec);
   for (int z = 1; z <= lat->dims[2]; ++z) {
     if (lat->dims[2] % z) continue;
-    if (2.0 * (lat->dims[2] / z) * plane <= 40.0e6) return z;
+    if (2.0 * (lat->dims[2] / z) * plane <= 20.0e6) return z;
   }
   return lat->dims[2];
 }
@@ -110,6 +111,10 @@ bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (t.variant < 0 || t.variant > kNumVariants - 1) return false;
   if (t.zblk < 1 || lat->dims[2] % t.zblk) return false;
   if (t.sgrp < 1 || (lat->Ls / t.spt) % t.sgrp || (op == OP_DDAG && t.sgrp != 1)) return false;
+  if (t.variant == 6 &&
+      (!rows_variant_ok(op, lat->dims[0], lat->dims[1], t.tx) ||
+       rows_smem_bytes(t.tx, lat->Ls / t.sgrp, prec) > 227 * 1024))
+    return false;
   const long long threads = (long long)t.tx * (lat->Ls / t.spt / t.sgrp);
   return threads <= 1024 && threads <= dslash_max_threads(prec, op, t.spt, t.variant);
 }
@@ -152,6 +157,7 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.halo_dn = halo_dn ? (const char *)halo_dn + (size_t)r0 * hrhs_bytes : nullptr;
     p.t_begin = t_begin;
     p.t_count = t_count;
+    p.status = lat->dev_status;
     p.M5 = lat->M5;
     p.b = lat->b;
     p.c = lat->c;
@@ -263,6 +269,12 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
       return fail(DW_ERR_ALLOC, "gauge allocation failed");
     }
   }
+  if (cudaMalloc(&lat->dev_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(lat->dev_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    dw_destroy_lattice(lat);
+    return fail(DW_ERR_ALLOC, "status word allocation failed");
+  }
   *out = lat;
   return DW_OK;
 }
@@ -275,6 +287,7 @@ void dw_destroy_lattice(dw_lattice *lat) {
   if (lat->stage_in) cudaFree(lat->stage_in);
   if (lat->stage_out) cudaFree(lat->stage_out);
   if (lat->partials) cudaFree(lat->partials);
+  if (lat->dev_status) cudaFree(lat->dev_status);
   cg_release(lat);
   pipe_release(lat);
   delete lat;
@@ -354,8 +367,9 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d sgrp=%d for Ls=%d Lz=%d (slices "
-                "per thread must divide Ls, tx a multiple of 32, variant 0..5, zblk dividing Lz, "
-                "sgrp dividing Ls/spt and 1 for D^+, CTA within the kernel's limits)",
+                "per thread must divide Ls, tx a multiple of 32, variant 0..6 (6: Lx = 32 and "
+                "Dhop only), zblk dividing Lz, sgrp dividing Ls/spt and 1 for D^+, CTA within "
+                "the kernel's limits)",
                 spt, tx, variant, zblk, sgrp, lat->Ls, lat->dims[2]);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;
   return DW_OK;
@@ -380,6 +394,18 @@ int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, 
   if (variant) *variant = t.variant;
   if (zblk) *zblk = t.zblk;
   if (sgrp) *sgrp = t.sgrp;
+  return DW_OK;
+}
+
+int dw_device_status(dw_lattice *lat) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, lat->dev_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemset(lat->dev_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (v) return fail(DW_ERR_TIMEOUT, "a stencil kernel gave up waiting for its shared-memory copies");
   return DW_OK;
 }
 

@@ -161,6 +161,7 @@ struct DslashParams {
   int sgrp;             // set by the launcher: CTAs per site tile (slice groups)
   int t_begin;          // output sites: the time slices t_begin .. t_begin + t_count - 1
   int t_count;          // (0: all Lt; the inputs are read on the whole lattice)
+  int *status;          // lattice-owned device word; set nonzero when a bounded wait gives up
   double M5, b, c;
   double mf[64];         // per-RHS masses, passed by value
 };
@@ -175,7 +176,20 @@ struct TileConfig {
   int zblk;     // z-blocks of the CTA traversal order (divides Lz)
   int sgrp;     // CTAs sharing one tile of sites, each with Ls / (spt sgrp) thread rows
 };
-constexpr int kNumVariants = 6;
+constexpr int kNumVariants = 7;
+
+// Variant 6 stages rows in shared memory: it needs Lx = 32 (a 32-site block is
+// one x row), tiles of whole rows that tile the (x, y) plane, the hopping term
+// alone (Dhop, Dhop^+) and no t halos.
+inline bool rows_variant_ok(int op, int Lx, int Ly, int tx) {
+  return (op == OP_DHOP || op == OP_DHOP_DAG) && Lx == 32 && tx % 32 == 0 && tx / 32 <= Ly &&
+         (Lx * Ly) % tx == 0;
+}
+// Dynamic shared memory of variant 6: the barrier, then rows y0-1 .. y0+R of
+// the CTA's nsl slices at precision `prec` (24 reals per site).
+inline size_t rows_smem_bytes(int tx, int nsl, int prec) {
+  return 128 + (size_t)(tx / 32 + 2) * nsl * 24 * 32 * prec_real_bytes(prec);
+}
 
 // Stencil launch at precision `prec`: 0 on success, -2 for a tile/variant
 // that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA
@@ -210,6 +224,7 @@ struct dw_lattice {
   int device;
   int num_sms;
   bool gauge_loaded;
+  int *dev_status;  // device word the kernels set when a bounded wait gives up
   // gauge copies per precision (blocked; 18 reals per link at FP64, 12 below)
   void *gauge[3];
   // scratch: one field for D^+D, host-apply staging, reduction partials

@@ -203,7 +203,8 @@ __device__ __forceinline__ void quad_in(double2 &re, double2 &im, const double2 
 // traversal a spinor is first touched as a t+ neighbour and last touched as a
 // t- neighbour: the first touch is kept (evict_last) for the reuses that follow
 // one or two slabs later, the last touch may leave first (evict_first).
-enum { HINT_NONE = 0, HINT_KEEP = 1, HINT_DROP = 2 };
+// HINT_SMEM marks a "field" that lives in shared memory (plain loads).
+enum { HINT_NONE = 0, HINT_KEEP = 1, HINT_DROP = 2, HINT_SMEM = 3 };
 template <int HINT>
 __device__ __forceinline__ unsigned long long l2_policy() {
   unsigned long long pol = 0;
@@ -236,6 +237,7 @@ __device__ __forceinline__ double2 ldg_hint(const double2 *p, unsigned long long
 }
 template <int HINT, class VEC>
 __device__ __forceinline__ VEC ld_vec(const VEC *p, unsigned long long pol) {
+  if (HINT == HINT_SMEM) return *p;
   if (HINT == HINT_NONE) return __ldg(p);
   return ldg_hint(p, pol);
 }
@@ -462,6 +464,44 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Bulk asynchronous copies (global -> shared, completion counted in bytes on
+// an mbarrier) for the row-staged variant.  Every wait is bounded.
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait for phase `parity` of the barrier; false after about a second or 2^24
+// polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (int i = 0; i < (1 << 24); ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+  return false;
 }
 
 template <class P, bool PHI, int SPT>
@@ -856,8 +896,10 @@ struct Hops {
 // registers spill more and ran slower at 32^3 x 64 x 12.)
 template <int VAR>
 struct RegCap {
-  static constexpr int value = VAR == 4 ? 128 : 0;
+  static constexpr int value = (VAR == 4 || VAR == 6) ? 128 : 0;
 };
+
+
 
 template <class P, int OP, int SPT, int VAR>
 __device__ __forceinline__ void dslash_body(const DslashParams &p) {
@@ -953,7 +995,69 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     }
   }
 
-  if (VAR == 0 || VAR >= 4) {
+  if (VAR == 6) {
+    // Rows path.  The tile is R = tx/32 whole x rows of one (z, t) plane; rows
+    // y0-1 .. y0+R of the CTA's slices (one contiguous run per row in the
+    // blocked layout) are bulk-copied into shared memory by one thread while
+    // the t and z hops run from global memory; the y and x hops then read
+    // their neighbours there.  Same hop order as variant 5, so the same sums.
+    constexpr int NPV = 24 / P::R;
+    const int nsl = nchunk * SPT;  // slices of this CTA
+    const int sbase = sg * nsl;
+    const int R = tx / 32;
+    const int Ly = p.L[1];
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw);
+    vec *rows = reinterpret_cast<vec *>(smem_raw + 128);
+    const int row_vecs = nsl * NPV * 32;
+    const int tid = threadIdx.y * tx + threadIdx.x;
+    const int y0 = (in_plane - (int)threadIdx.x) >> 5;  // first row of the tile
+    const int plane_blk = (x4 - in_plane) >> 5;          // block of row 0 of the plane
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned bytes = (unsigned)(row_vecs * sizeof(vec));
+      mbar_expect_tx(bar, bytes * (unsigned)(R + 2));
+      for (int r = 0; r < R + 2; ++r) {
+        int y = y0 - 1 + r;
+        y = y < 0 ? y + Ly : (y >= Ly ? y - Ly : y);
+        const vec *src = F.base + ((long long)(plane_blk + y) * Ls + sbase) * NPV * 32;
+        bulk_g2s(rows + (size_t)r * row_vecs, src, bytes, bar);
+      }
+    }
+    const Hops H(p, x4);
+    hop_dir<P, 3, SF, false, false, true, SPT, HINT_KEEP>(acc, F, gauge, (C)H.sign<3, true>(p),
+                                                         H.nb<3, true>(p), x4, s0, Ls, b, c, mf);
+    hop_dir<P, 3, SB, true, false, false, SPT, HINT_DROP>(acc, F, gauge, (C)H.sign<3, false>(p),
+                                                          H.nb<3, false>(p), H.nb<3, false>(p),
+                                                          s0, Ls, b, c, mf);
+    hop_dir<P, 2, SF, false, false, false, SPT>(acc, F, gauge, (C)H.sign<2, true>(p),
+                                                H.nb<2, true>(p), x4, s0, Ls, b, c, mf);
+    hop_dir<P, 2, SB, true, false, false, SPT>(acc, F, gauge, (C)H.sign<2, false>(p),
+                                               H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls, b,
+                                               c, mf);
+    if (!mbar_wait(bar, 0)) {
+      atomicExch(p.status, 1);
+      mbar_wait(bar, 0);  // one more bounded wait for the copies in flight
+      return;
+    }
+    Field<P> S;  // the staged rows, addressed as blocks of 32 sites x nsl slices
+    S.base = rows;
+    S.V4 = 0;
+    S.Ls = nsl;
+    const int ry = (in_plane >> 5) - y0;  // row of this site in the tile
+    const int xl = in_plane & 31;
+    const int sl = s0 - sbase;
+    hop_dir<P, 1, SF, false, false, false, SPT, HINT_SMEM>(
+        acc, S, gauge, (C)H.sign<1, true>(p), (ry + 2) * 32 + xl, x4, sl, nsl, b, c, mf);
+    hop_dir<P, 1, SB, true, false, false, SPT, HINT_SMEM>(
+        acc, S, gauge, (C)H.sign<1, false>(p), ry * 32 + xl, H.nb<1, false>(p), sl, nsl, b, c, mf);
+    hop_dir<P, 0, SF, false, false, false, SPT, HINT_SMEM>(
+        acc, S, gauge, (C)H.sign<0, true>(p), (ry + 1) * 32 + ((xl + 1) & 31), x4, sl, nsl, b, c,
+        mf);
+    hop_dir<P, 0, SB, true, false, false, SPT, HINT_SMEM>(
+        acc, S, gauge, (C)H.sign<0, false>(p), (ry + 1) * 32 + ((xl + 31) & 31), H.nb<0, false>(p),
+        sl, nsl, b, c, mf);
+  } else if (VAR == 0 || VAR == 4 || VAR == 5) {
     if (active) {
       const Hops H(p, x4);
       // t faces of a sub-lattice take their t-neighbours from the halos
@@ -1138,6 +1242,7 @@ template <class P, int OP, int SPT, int VAR>
 size_t dslash_smem(int tx, int nchunk) {
   size_t smem = 0;
   if (VAR == 1) smem += kStages * StageLayout<P, OP == OP_D, SPT>::stage_bytes(tx * nchunk);
+  if (VAR == 6) smem += rows_smem_bytes(tx, nchunk * SPT, P::id);
   if (OP == OP_DDAG) smem += 2 * (size_t)nchunk * 12 * tx * sizeof(typename P::C);  // 6 pairs
   return smem;
 }
@@ -1153,6 +1258,7 @@ int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t s
   q.zblk = zblk;
   q.sgrp = sgrp;
   if (zblk < 1 || p.L[2] % zblk) return -2;
+  if (VAR == 6 && (!rows_variant_ok(OP, p.L[0], p.L[1], tx) || p.halo_up || p.halo_dn)) return -2;
   if (q.t_count == 0) {
     q.t_begin = 0;
     q.t_count = p.L[3];

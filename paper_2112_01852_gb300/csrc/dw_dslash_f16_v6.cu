@@ -1,0 +1,4 @@
+// F16 storage, hop-phase variant 6 (x and y neighbour rows staged in shared memory by bulk copies).
+#include "dw_dslash.cuh"
+
+DW_DSLASH_INSTANTIATE(F16, 6)

@@ -32,7 +32,6 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
           for (int sgrp : {1, 2, 3, 4, 6}) {
             TileConfig t{spt, tx, variant, zblk, sgrp};
             if (zblk != 1 && zblk != za) continue;  // unblocked and the automatic blocking
-            if (sgrp > 1 && tx > 32) continue;      // split only the narrowest CTAs
             if (quick && (tx > 64 || zblk != za || sgrp > 2)) continue;
             if (!tile_valid(lat, prec, op, t)) continue;
             // warm-up launch doubles as the validity check

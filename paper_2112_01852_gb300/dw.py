@@ -52,8 +52,8 @@ SYMBOLS = (
     "dw_create_lattice", "dw_destroy_lattice", "dw_load_gauge", "dw_apply_Dhop",
     "dw_apply_Dhop_dag", "dw_apply_D", "dw_apply_Ddag", "dw_apply_DdagD",
     "dw_apply_DdagD_noalloc", "dw_apply_host",
-    "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_halo_bytes", "dw_halo_pack",
-    "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
+    "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_device_status", "dw_halo_bytes",
+    "dw_halo_pack", "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
     "dw_unpack_fermion", "dw_last_error",
 )
 
@@ -106,6 +106,7 @@ def load_library():
             "dw_cg_solve": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
             "dw_set_tile": (I, [P, I, I, I, I, I, I, I, I]),
             "dw_tune": (I, [P, I, I, IP, IP, IP, IP, IP, P]),
+            "dw_device_status": (I, [P]),
             "dw_halo_bytes": (S, [P, I, I]),
             "dw_halo_pack": (I, [P, P, P, P, I, I, P]),
             "dw_apply_Dhop_halo": (I, [P, P, P, P, P, I, I, P]),
@@ -212,6 +213,11 @@ def dw_tune(lat, op, nrhs, stream=0):
     _check(load_library().dw_tune(lat, int(op), int(nrhs), *[ctypes.byref(v) for v in vals],
                                   stream))
     return tuple(v.value for v in vals)
+
+
+def dw_device_status(lat):
+    """Raises DWError (DW_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
+    _check(load_library().dw_device_status(lat))
 
 
 def dw_halo_bytes(lat, prec, nrhs):

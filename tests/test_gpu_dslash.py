@@ -82,7 +82,7 @@ def test_all_tiles_ragged(Ls):
     lat.load_gauge(U)
     refs = {op: run_oracle(op, psi, U, dims, Ls, 1.6, 1.25, 0.75, mfs, bc) for op in STENCIL_OPS}
     ran = set()
-    for variant in range(6):
+    for variant in range(7):
         for spt, tx in valid_tiles(Ls):
             for op in STENCIL_OPS:
                 try:
@@ -110,7 +110,7 @@ def test_slice_groups_equal_one_cta(prec):
     lat.load_gauge(U)
     ran = 0
     for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG, dw.DW_OP_D):
-        for variant in range(6):
+        for variant in range(7):
             for spt in (1, 2, 3):
                 try:
                     lat.set_tile(op, spt, 32, variant)
@@ -125,6 +125,53 @@ def test_slice_groups_equal_one_cta(prec):
                     assert np.array_equal(got, ref), (OP_NAMES[op], variant, spt, sgrp)
                     ran += 1
     assert ran > 0
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [dw.DW_F32, dw.DW_F16], ids=["f32", "f16"])
+@pytest.mark.parametrize("dims", [(32, 4, 2, 6), (32, 2, 2, 4), (32, 1, 2, 4)],
+                         ids=["Ly4", "Ly2", "Ly1"])
+def test_row_staged_variant(prec, dims):
+    # variant 6 reads the x and y neighbours from rows staged in shared memory;
+    # it sums the same terms in the same order as variant 5: equal bit for bit,
+    # and within tolerance of the oracle.  Ly = 2 and 1: the halo rows repeat
+    # rows of the tile.
+    Ls = 4
+    U, psi = make_case(dims, Ls, 2, seed=17)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
+    lat.load_gauge(U)
+    ran = 0
+    for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG):
+        ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.0, 0.0])
+        for spt in (1, 2):
+            lat.set_tile(op, spt, 32, 5)
+            v5 = run_gpu(lat, op, psi)
+            for tx in (32, 64, 128):
+                for sgrp in (1, 2, 4):
+                    try:
+                        lat.set_tile(op, spt, tx, 6, sgrp=sgrp)
+                    except dw.DWError as e:
+                        assert e.code == dw.DW_ERR_ARG
+                        continue
+                    got = run_gpu(lat, op, psi)
+                    assert np.array_equal(got, v5), (OP_NAMES[op], spt, tx, sgrp)
+                    assert max_rel(got, ref) <= TOL[prec]
+                    ran += 1
+    dw.dw_device_status(lat.handle)
+    assert ran >= 8
+    with pytest.raises(dw.DWError):  # D is not a hopping-only operator
+        lat.set_tile(dw.DW_OP_D, 1, 32, 6)
+    lat.close()
+
+
+def test_row_staged_variant_needs_lx32():
+    dims, Ls = (16, 4, 2, 4), 4
+    U, _ = make_case(dims, Ls, 1, seed=18)
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
+    lat.load_gauge(U)
+    with pytest.raises(dw.DWError) as e:
+        lat.set_tile(dw.DW_OP_DHOP, 1, 32, 6)
+    assert e.value.code == dw.DW_ERR_ARG
     lat.close()
 
 
@@ -150,7 +197,7 @@ def test_both_variants_low_precision(prec):
     lat.load_gauge(U)
     refs = {op: run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mfs) for op in STENCIL_OPS}
     ran = set()
-    for variant in range(6):
+    for variant in range(7):
         for spt in (1, 2, 3, 4):
             for op in STENCIL_OPS:
                 try:
@@ -160,7 +207,7 @@ def test_both_variants_low_precision(prec):
                 ran.add((variant, op))
                 got = run_gpu(lat, op, psi, mf=mfs)
                 assert max_rel(got, refs[op]) <= TOL[prec], (OP_NAMES[op], spt, variant)
-    built = tuple(range(6))
+    built = tuple(range(6))  # variant 6 needs Lx = 32: its own test below
     assert {(v, op) for v in built for op in STENCIL_OPS} <= ran
     lat.close()
 
@@ -283,7 +330,7 @@ def test_tune_picks_valid_tile_and_stays_exact():
         assert dims[2] % zblk == 0
         assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
         assert (Ls // spt) % sgrp == 0 and (sgrp == 1 or op != dw.DW_OP_DDAG)
-        assert variant in range(6)
+        assert variant in range(7)
         got = run_gpu(lat, op, psi, mf=[0.01])
         ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
         assert max_rel(got, ref) <= TOL[dw.DW_F32], OP_NAMES[op]
