@@ -1024,17 +1024,19 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         bulk_g2s(rows + (size_t)r * row_vecs, src, bytes, bar);
       }
     }
+    const C zero = C(0);  // the hopping term alone: no (b + cK) combination
     const Hops H(p, x4);
-    hop_dir<P, 3, SF, false, false, true, SPT, HINT_KEEP>(acc, F, gauge, (C)H.sign<3, true>(p),
-                                                         H.nb<3, true>(p), x4, s0, Ls, b, c, mf);
+    hop_dir<P, 3, SF, false, false, true, SPT, HINT_KEEP>(
+        acc, F, gauge, (C)H.sign<3, true>(p), H.nb<3, true>(p), x4, s0, Ls, zero, zero, zero);
     hop_dir<P, 3, SB, true, false, false, SPT, HINT_DROP>(acc, F, gauge, (C)H.sign<3, false>(p),
                                                           H.nb<3, false>(p), H.nb<3, false>(p),
-                                                          s0, Ls, b, c, mf);
+                                                          s0, Ls, zero, zero, zero);
     hop_dir<P, 2, SF, false, false, false, SPT>(acc, F, gauge, (C)H.sign<2, true>(p),
-                                                H.nb<2, true>(p), x4, s0, Ls, b, c, mf);
+                                                H.nb<2, true>(p), x4, s0, Ls, zero, zero,
+                                                zero);
     hop_dir<P, 2, SB, true, false, false, SPT>(acc, F, gauge, (C)H.sign<2, false>(p),
-                                               H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls, b,
-                                               c, mf);
+                                               H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls, zero,
+                                               zero, zero);
     if (!mbar_wait(bar, 0)) {
       atomicExch(p.status, 1);
       mbar_wait(bar, 0);  // one more bounded wait for the copies in flight
@@ -1046,17 +1048,19 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     S.Ls = nsl;
     const int ry = (in_plane >> 5) - y0;  // row of this site in the tile
     const int xl = in_plane & 31;
-    const int sl = s0 - sbase;
+    const int sl = (int)threadIdx.y * SPT;  // = s0 - sbase
     hop_dir<P, 1, SF, false, false, false, SPT, HINT_SMEM>(
-        acc, S, gauge, (C)H.sign<1, true>(p), (ry + 2) * 32 + xl, x4, sl, nsl, b, c, mf);
+        acc, S, gauge, (C)H.sign<1, true>(p), (ry + 2) * 32 + xl, x4, sl, nsl, zero, zero,
+        zero);
     hop_dir<P, 1, SB, true, false, false, SPT, HINT_SMEM>(
-        acc, S, gauge, (C)H.sign<1, false>(p), ry * 32 + xl, H.nb<1, false>(p), sl, nsl, b, c, mf);
+        acc, S, gauge, (C)H.sign<1, false>(p), ry * 32 + xl, H.nb<1, false>(p), sl, nsl, zero,
+        zero, zero);
     hop_dir<P, 0, SF, false, false, false, SPT, HINT_SMEM>(
-        acc, S, gauge, (C)H.sign<0, true>(p), (ry + 1) * 32 + ((xl + 1) & 31), x4, sl, nsl, b, c,
-        mf);
+        acc, S, gauge, (C)H.sign<0, true>(p), (ry + 1) * 32 + ((xl + 1) & 31), x4, sl, nsl, zero,
+        zero, zero);
     hop_dir<P, 0, SB, true, false, false, SPT, HINT_SMEM>(
         acc, S, gauge, (C)H.sign<0, false>(p), (ry + 1) * 32 + ((xl + 31) & 31), H.nb<0, false>(p),
-        sl, nsl, b, c, mf);
+        sl, nsl, zero, zero, zero);
   } else if (VAR == 0 || VAR == 4 || VAR == 5) {
     if (active) {
       const Hops H(p, x4);
