@@ -196,7 +196,10 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
  * 128 registers per thread; 6 = variant 4 with the tile's x rows and their two
  * y-neighbour rows bulk-copied into shared memory, the x and y hops read there
  * (needs Lx = 32, tx dividing Lx*Ly, DW_OP_DHOP / DW_OP_DHOP_DAG only; its
- * bounded wait reports through dw_device_status); FP64 builds 0 and 2 only), zblk, the
+ * bounded wait reports through dw_device_status); 7 = variant 6 with one CTA
+ * walking all tiles of its (z, t) plane in y, the rows kept in a ring so that
+ * each row is copied once per plane (same conditions); FP64 builds 0 and 2
+ * only), zblk, the
  * number of z-blocks of the CTA traversal order (planes are visited block by
  * block, t inside a block; zblk divides Lz; 0 in dw_set_tile = automatic), and
  * sgrp, the number of CTAs that share one tile of tx sites: each holds

@@ -111,7 +111,7 @@ bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (t.variant < 0 || t.variant > kNumVariants - 1) return false;
   if (t.zblk < 1 || lat->dims[2] % t.zblk) return false;
   if (t.sgrp < 1 || (lat->Ls / t.spt) % t.sgrp || (op == OP_DDAG && t.sgrp != 1)) return false;
-  if (t.variant == 6 &&
+  if ((t.variant == 6 || t.variant == 7) &&
       (!rows_variant_ok(op, lat->dims[0], lat->dims[1], t.tx) ||
        rows_smem_bytes(t.tx, lat->Ls / t.sgrp, prec) > 227 * 1024))
     return false;
@@ -127,7 +127,8 @@ size_t halo_bytes(const dw_lattice *lat, int prec, int nrhs) {
 
 // CTAs per right-hand side of a stencil launch with tile `t`.
 long long dslash_ctas_per_rhs(const dw_lattice *lat, TileConfig t) {
-  const long long per_plane = ((long long)lat->dims[0] * lat->dims[1] + t.tx - 1) / t.tx;
+  const long long per_plane =
+      t.variant == 7 ? 1 : ((long long)lat->dims[0] * lat->dims[1] + t.tx - 1) / t.tx;
   return per_plane * t.sgrp * lat->dims[2] * lat->dims[3];
 }
 
@@ -367,7 +368,7 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d sgrp=%d for Ls=%d Lz=%d (slices "
-                "per thread must divide Ls, tx a multiple of 32, variant 0..6 (6: Lx = 32 and "
+                "per thread must divide Ls, tx a multiple of 32, variant 0..7 (6, 7: Lx = 32 and "
                 "Dhop only), zblk dividing Lz, sgrp dividing Ls/spt and 1 for D^+, CTA within "
                 "the kernel's limits)",
                 spt, tx, variant, zblk, sgrp, lat->Ls, lat->dims[2]);

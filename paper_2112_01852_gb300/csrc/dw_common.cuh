@@ -176,17 +176,18 @@ struct TileConfig {
   int zblk;     // z-blocks of the CTA traversal order (divides Lz)
   int sgrp;     // CTAs sharing one tile of sites, each with Ls / (spt sgrp) thread rows
 };
-constexpr int kNumVariants = 7;
+constexpr int kNumVariants = 8;
 
-// Variant 6 stages rows in shared memory: it needs Lx = 32 (a 32-site block is
-// one x row), tiles of whole rows that tile the (x, y) plane, the hopping term
-// alone (Dhop, Dhop^+) and no t halos.
+// Variants 6 and 7 stage rows in shared memory: they need Lx = 32 (a 32-site
+// block is one x row), tiles of whole rows that tile the (x, y) plane, the
+// hopping term alone (Dhop, Dhop^+) and no t halos.
 inline bool rows_variant_ok(int op, int Lx, int Ly, int tx) {
   return (op == OP_DHOP || op == OP_DHOP_DAG) && Lx == 32 && tx % 32 == 0 && tx / 32 <= Ly &&
          (Lx * Ly) % tx == 0;
 }
-// Dynamic shared memory of variant 6: the barrier, then rows y0-1 .. y0+R of
-// the CTA's nsl slices at precision `prec` (24 reals per site).
+// Dynamic shared memory of variants 6 and 7: the barrier, then R + 2 rows
+// (y0-1 .. y0+R, or the ring slots) of the CTA's nsl slices at precision
+// `prec` (24 reals per site).
 inline size_t rows_smem_bytes(int tx, int nsl, int prec) {
   return 128 + (size_t)(tx / 32 + 2) * nsl * 24 * 32 * prec_real_bytes(prec);
 }

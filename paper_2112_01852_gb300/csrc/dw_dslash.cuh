@@ -896,7 +896,7 @@ struct Hops {
 // registers spill more and ran slower at 32^3 x 64 x 12.)
 template <int VAR>
 struct RegCap {
-  static constexpr int value = (VAR == 4 || VAR == 6) ? 128 : 0;
+  static constexpr int value = (VAR == 4 || VAR == 6 || VAR == 7) ? 128 : 0;
 };
 
 
@@ -995,72 +995,99 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     }
   }
 
-  if (VAR == 6) {
-    // Rows path.  The tile is R = tx/32 whole x rows of one (z, t) plane; rows
+  if (VAR == 6 || VAR == 7) {
+    // Rows path.  A tile is R = tx/32 whole x rows of one (z, t) plane; rows
     // y0-1 .. y0+R of the CTA's slices (one contiguous run per row in the
     // blocked layout) are bulk-copied into shared memory by one thread while
     // the t and z hops run from global memory; the y and x hops then read
     // their neighbours there.  Same hop order as variant 5, so the same sums.
+    // Variant 6: one tile per CTA.  Variant 7: the CTA walks the Ly/R tiles of
+    // its plane in y, keeping the rows in a ring of R + 2 slots (row v in slot
+    // (v + 1) mod (R + 2)): each step copies only its R new rows, the two rows
+    // shared with the previous tile stay.
+    constexpr bool RING = (VAR == 7);
     constexpr int NPV = 24 / P::R;
     const int nsl = nchunk * SPT;  // slices of this CTA
     const int sbase = sg * nsl;
     const int R = tx / 32;
     const int Ly = p.L[1];
+    const int NR = R + 2;  // row slots
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw);
     vec *rows = reinterpret_cast<vec *>(smem_raw + 128);
     const int row_vecs = nsl * NPV * 32;
-    const int tid = threadIdx.y * tx + threadIdx.x;
-    const int y0 = (in_plane - (int)threadIdx.x) >> 5;  // first row of the tile
-    const int plane_blk = (x4 - in_plane) >> 5;          // block of row 0 of the plane
-    if (tid == 0) mbar_init(bar, 1);
+    const unsigned row_bytes = (unsigned)(row_vecs * sizeof(vec));
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const int plane_base = x4 - in_plane;  // x4 of site 0 of the plane
+    const int plane_blk = plane_base >> 5;  // block of row 0 of the plane
+    const int steps = RING ? (p.L[0] * Ly) / tx : 1;
+    const C zero = C(0);  // the hopping term alone: no (b + cK) combination
+    const int sl = (int)threadIdx.y * SPT;  // = s0 - sbase
+    if (leader) mbar_init(bar, 1);
     __syncthreads();
-    if (tid == 0) {
-      const unsigned bytes = (unsigned)(row_vecs * sizeof(vec));
-      mbar_expect_tx(bar, bytes * (unsigned)(R + 2));
-      for (int r = 0; r < R + 2; ++r) {
-        int y = y0 - 1 + r;
-        y = y < 0 ? y + Ly : (y >= Ly ? y - Ly : y);
-        const vec *src = F.base + ((long long)(plane_blk + y) * Ls + sbase) * NPV * 32;
-        bulk_g2s(rows + (size_t)r * row_vecs, src, bytes, bar);
+    for (int k = 0; k < steps; ++k) {
+      const int ip = RING ? k * tx + (int)threadIdx.x : in_plane;  // site in the plane
+      const int xs = plane_base + ip;
+      const int y0 = (ip - (int)threadIdx.x) >> 5;  // first row of the tile
+      if (leader) {
+        // rows y0-1 .. y0+R (all of them at the first step; the ring keeps
+        // two and takes R new ones later); rows are taken periodically in y
+        const int first = (RING && k > 0) ? y0 + 1 : y0 - 1;
+        const int n = (RING && k > 0) ? R : R + 2;
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(bar, row_bytes * (unsigned)n);
+        for (int r = 0; r < n; ++r) {
+          const int v = first + r;  // virtual row, -1 .. Ly
+          const int y = v < 0 ? v + Ly : (v >= Ly ? v - Ly : v);
+          const int slot = RING ? (v + 1) % NR : r;
+          const vec *src = F.base + ((long long)(plane_blk + y) * Ls + sbase) * NPV * 32;
+          bulk_g2s(rows + (size_t)slot * row_vecs, src, row_bytes, bar);
+        }
+      }
+      const Hops H(p, xs);
+      hop_dir<P, 3, SF, false, false, true, SPT, HINT_KEEP>(
+          acc, F, gauge, (C)H.sign<3, true>(p), H.nb<3, true>(p), xs, s0, Ls, zero, zero, zero);
+      hop_dir<P, 3, SB, true, false, false, SPT, HINT_DROP>(
+          acc, F, gauge, (C)H.sign<3, false>(p), H.nb<3, false>(p), H.nb<3, false>(p), s0, Ls,
+          zero, zero, zero);
+      hop_dir<P, 2, SF, false, false, false, SPT>(acc, F, gauge, (C)H.sign<2, true>(p),
+                                                  H.nb<2, true>(p), xs, s0, Ls, zero, zero,
+                                                  zero);
+      hop_dir<P, 2, SB, true, false, false, SPT>(acc, F, gauge, (C)H.sign<2, false>(p),
+                                                 H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls,
+                                                 zero, zero, zero);
+      if (!mbar_wait(bar, (unsigned)k & 1u)) {
+        atomicExch(p.status, 1);
+        mbar_wait(bar, (unsigned)k & 1u);  // one more bounded wait for the copies in flight
+      }
+      Field<P> S;  // the staged rows, addressed as blocks of 32 sites x nsl slices
+      S.base = rows;
+      S.V4 = 0;
+      S.Ls = nsl;
+      const int ry = (ip >> 5) - y0;  // row of this site in the tile
+      const int xl = ip & 31;
+      // slots of the rows below, at and above this site's row
+      const int sdn = RING ? (y0 + ry) % NR : ry;
+      const int sat = RING ? (y0 + ry + 1) % NR : ry + 1;
+      const int sup = RING ? (y0 + ry + 2) % NR : ry + 2;
+      hop_dir<P, 1, SF, false, false, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<1, true>(p), sup * 32 + xl, xs, sl, nsl, zero, zero, zero);
+      hop_dir<P, 1, SB, true, false, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<1, false>(p), sdn * 32 + xl, H.nb<1, false>(p), sl, nsl, zero,
+          zero, zero);
+      hop_dir<P, 0, SF, false, false, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<0, true>(p), sat * 32 + ((xl + 1) & 31), xs, sl, nsl, zero,
+          zero, zero);
+      hop_dir<P, 0, SB, true, false, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<0, false>(p), sat * 32 + ((xl + 31) & 31), H.nb<0, false>(p),
+          sl, nsl, zero, zero, zero);
+      if (RING) {
+#pragma unroll
+        for (int j = 0; j < SPT; ++j)
+          store_spinor<P>(out + F.site(s0 + j, xs), kPlaneStride, acc[j]);
+        __syncthreads();  // every thread is done with the slots the next step refills
       }
     }
-    const C zero = C(0);  // the hopping term alone: no (b + cK) combination
-    const Hops H(p, x4);
-    hop_dir<P, 3, SF, false, false, true, SPT, HINT_KEEP>(
-        acc, F, gauge, (C)H.sign<3, true>(p), H.nb<3, true>(p), x4, s0, Ls, zero, zero, zero);
-    hop_dir<P, 3, SB, true, false, false, SPT, HINT_DROP>(acc, F, gauge, (C)H.sign<3, false>(p),
-                                                          H.nb<3, false>(p), H.nb<3, false>(p),
-                                                          s0, Ls, zero, zero, zero);
-    hop_dir<P, 2, SF, false, false, false, SPT>(acc, F, gauge, (C)H.sign<2, true>(p),
-                                                H.nb<2, true>(p), x4, s0, Ls, zero, zero,
-                                                zero);
-    hop_dir<P, 2, SB, true, false, false, SPT>(acc, F, gauge, (C)H.sign<2, false>(p),
-                                               H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls, zero,
-                                               zero, zero);
-    if (!mbar_wait(bar, 0)) {
-      atomicExch(p.status, 1);
-      mbar_wait(bar, 0);  // one more bounded wait for the copies in flight
-      return;
-    }
-    Field<P> S;  // the staged rows, addressed as blocks of 32 sites x nsl slices
-    S.base = rows;
-    S.V4 = 0;
-    S.Ls = nsl;
-    const int ry = (in_plane >> 5) - y0;  // row of this site in the tile
-    const int xl = in_plane & 31;
-    const int sl = (int)threadIdx.y * SPT;  // = s0 - sbase
-    hop_dir<P, 1, SF, false, false, false, SPT, HINT_SMEM>(
-        acc, S, gauge, (C)H.sign<1, true>(p), (ry + 2) * 32 + xl, x4, sl, nsl, zero, zero,
-        zero);
-    hop_dir<P, 1, SB, true, false, false, SPT, HINT_SMEM>(
-        acc, S, gauge, (C)H.sign<1, false>(p), ry * 32 + xl, H.nb<1, false>(p), sl, nsl, zero,
-        zero, zero);
-    hop_dir<P, 0, SF, false, false, false, SPT, HINT_SMEM>(
-        acc, S, gauge, (C)H.sign<0, true>(p), (ry + 1) * 32 + ((xl + 1) & 31), x4, sl, nsl, zero,
-        zero, zero);
-    hop_dir<P, 0, SB, true, false, false, SPT, HINT_SMEM>(
-        acc, S, gauge, (C)H.sign<0, false>(p), (ry + 1) * 32 + ((xl + 31) & 31), H.nb<0, false>(p),
-        sl, nsl, zero, zero, zero);
+    if (RING) return;
   } else if (VAR == 0 || VAR == 4 || VAR == 5) {
     if (active) {
       const Hops H(p, x4);
@@ -1246,7 +1273,7 @@ template <class P, int OP, int SPT, int VAR>
 size_t dslash_smem(int tx, int nchunk) {
   size_t smem = 0;
   if (VAR == 1) smem += kStages * StageLayout<P, OP == OP_D, SPT>::stage_bytes(tx * nchunk);
-  if (VAR == 6) smem += rows_smem_bytes(tx, nchunk * SPT, P::id);
+  if (VAR == 6 || VAR == 7) smem += rows_smem_bytes(tx, nchunk * SPT, P::id);
   if (OP == OP_DDAG) smem += 2 * (size_t)nchunk * 12 * tx * sizeof(typename P::C);  // 6 pairs
   return smem;
 }
@@ -1258,11 +1285,14 @@ int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t s
   const int nchunk = p.Ls / SPT / sgrp;
   dim3 block(tx, nchunk);
   DslashParams q = p;
-  q.tiles_per_plane = (p.L[0] * p.L[1] + tx - 1) / tx;
+  // variant 7: one CTA per plane (it walks the plane's tiles itself)
+  q.tiles_per_plane = VAR == 7 ? 1 : (p.L[0] * p.L[1] + tx - 1) / tx;
   q.zblk = zblk;
   q.sgrp = sgrp;
   if (zblk < 1 || p.L[2] % zblk) return -2;
-  if (VAR == 6 && (!rows_variant_ok(OP, p.L[0], p.L[1], tx) || p.halo_up || p.halo_dn)) return -2;
+  if ((VAR == 6 || VAR == 7) &&
+      (!rows_variant_ok(OP, p.L[0], p.L[1], tx) || p.halo_up || p.halo_dn))
+    return -2;
   if (q.t_count == 0) {
     q.t_begin = 0;
     q.t_count = p.L[3];

@@ -23,6 +23,8 @@ int launch_dslash_F32_v5(const DslashParams &p, int op, TileConfig cfg, cudaStre
 int dslash_max_threads_F32_v5(int op, int spt);
 int launch_dslash_F32_v6(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F32_v6(int op, int spt);
+int launch_dslash_F32_v7(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F32_v7(int op, int spt);
 int launch_dslash_F16_v0(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v0(int op, int spt);
 int launch_dslash_F16_v1(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
@@ -37,6 +39,8 @@ int launch_dslash_F16_v5(const DslashParams &p, int op, TileConfig cfg, cudaStre
 int dslash_max_threads_F16_v5(int op, int spt);
 int launch_dslash_F16_v6(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v6(int op, int spt);
+int launch_dslash_F16_v7(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int dslash_max_threads_F16_v7(int op, int spt);
 
 int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st) {
   const int cfg_variant = cfg.variant;
@@ -56,6 +60,7 @@ int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaS
         case 4: return launch_dslash_F32_v4(p, op, cfg, st);
         case 5: return launch_dslash_F32_v5(p, op, cfg, st);
         case 6: return launch_dslash_F32_v6(p, op, cfg, st);
+        case 7: return launch_dslash_F32_v7(p, op, cfg, st);
         default: return -2;
       }
     case DW_F16:
@@ -67,6 +72,7 @@ int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaS
         case 4: return launch_dslash_F16_v4(p, op, cfg, st);
         case 5: return launch_dslash_F16_v5(p, op, cfg, st);
         case 6: return launch_dslash_F16_v6(p, op, cfg, st);
+        case 7: return launch_dslash_F16_v7(p, op, cfg, st);
         default: return -2;
       }
   }
@@ -91,6 +97,7 @@ int dslash_max_threads(int prec, int op, int spt, int variant) {
         case 4: return dslash_max_threads_F32_v4(op, spt);
         case 5: return dslash_max_threads_F32_v5(op, spt);
         case 6: return dslash_max_threads_F32_v6(op, spt);
+        case 7: return dslash_max_threads_F32_v7(op, spt);
         default: return 0;
       }
     case DW_F16:
@@ -102,6 +109,7 @@ int dslash_max_threads(int prec, int op, int spt, int variant) {
         case 4: return dslash_max_threads_F16_v4(op, spt);
         case 5: return dslash_max_threads_F16_v5(op, spt);
         case 6: return dslash_max_threads_F16_v6(op, spt);
+        case 7: return dslash_max_threads_F16_v7(op, spt);
         default: return 0;
       }
   }

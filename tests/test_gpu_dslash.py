@@ -5,6 +5,8 @@ Tolerances (relative L2 over each right-hand side): 1e-12 at FP64, 1e-5 at
 FP32 storage, 5e-3 at FP16 storage.
 """
 
+import itertools
+
 import numpy as np
 import pytest
 
@@ -82,7 +84,7 @@ def test_all_tiles_ragged(Ls):
     lat.load_gauge(U)
     refs = {op: run_oracle(op, psi, U, dims, Ls, 1.6, 1.25, 0.75, mfs, bc) for op in STENCIL_OPS}
     ran = set()
-    for variant in range(7):
+    for variant in range(8):
         for spt, tx in valid_tiles(Ls):
             for op in STENCIL_OPS:
                 try:
@@ -110,7 +112,7 @@ def test_slice_groups_equal_one_cta(prec):
     lat.load_gauge(U)
     ran = 0
     for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG, dw.DW_OP_D):
-        for variant in range(7):
+        for variant in range(8):
             for spt in (1, 2, 3):
                 try:
                     lat.set_tile(op, spt, 32, variant)
@@ -132,10 +134,11 @@ def test_slice_groups_equal_one_cta(prec):
 @pytest.mark.parametrize("dims", [(32, 4, 2, 6), (32, 2, 2, 4), (32, 1, 2, 4)],
                          ids=["Ly4", "Ly2", "Ly1"])
 def test_row_staged_variant(prec, dims):
-    # variant 6 reads the x and y neighbours from rows staged in shared memory;
-    # it sums the same terms in the same order as variant 5: equal bit for bit,
-    # and within tolerance of the oracle.  Ly = 2 and 1: the halo rows repeat
-    # rows of the tile.
+    # variants 6 and 7 read the x and y neighbours from rows staged in shared
+    # memory (7 walking the plane's tiles with a ring of rows); they sum the
+    # same terms in the same order as variant 5: equal bit for bit, and within
+    # tolerance of the oracle.  Ly = 2 and 1: the halo rows repeat rows of the
+    # tile (and the ring wraps within one step).
     Ls = 4
     U, psi = make_case(dims, Ls, 2, seed=17)
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
@@ -146,21 +149,21 @@ def test_row_staged_variant(prec, dims):
         for spt in (1, 2):
             lat.set_tile(op, spt, 32, 5)
             v5 = run_gpu(lat, op, psi)
-            for tx in (32, 64, 128):
-                for sgrp in (1, 2, 4):
-                    try:
-                        lat.set_tile(op, spt, tx, 6, sgrp=sgrp)
-                    except dw.DWError as e:
-                        assert e.code == dw.DW_ERR_ARG
-                        continue
-                    got = run_gpu(lat, op, psi)
-                    assert np.array_equal(got, v5), (OP_NAMES[op], spt, tx, sgrp)
-                    assert max_rel(got, ref) <= TOL[prec]
-                    ran += 1
+            for var, tx, sgrp in itertools.product((6, 7), (32, 64, 128), (1, 2, 4)):
+                try:
+                    lat.set_tile(op, spt, tx, var, sgrp=sgrp)
+                except dw.DWError as e:
+                    assert e.code == dw.DW_ERR_ARG
+                    continue
+                got = run_gpu(lat, op, psi)
+                assert np.array_equal(got, v5), (OP_NAMES[op], spt, tx, var, sgrp)
+                assert max_rel(got, ref) <= TOL[prec]
+                ran += 1
     dw.dw_device_status(lat.handle)
-    assert ran >= 8
-    with pytest.raises(dw.DWError):  # D is not a hopping-only operator
-        lat.set_tile(dw.DW_OP_D, 1, 32, 6)
+    assert ran >= 16
+    for var in (6, 7):
+        with pytest.raises(dw.DWError):  # D is not a hopping-only operator
+            lat.set_tile(dw.DW_OP_D, 1, 32, var)
     lat.close()
 
 
@@ -169,9 +172,10 @@ def test_row_staged_variant_needs_lx32():
     U, _ = make_case(dims, Ls, 1, seed=18)
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
     lat.load_gauge(U)
-    with pytest.raises(dw.DWError) as e:
-        lat.set_tile(dw.DW_OP_DHOP, 1, 32, 6)
-    assert e.value.code == dw.DW_ERR_ARG
+    for var in (6, 7):
+        with pytest.raises(dw.DWError) as e:
+            lat.set_tile(dw.DW_OP_DHOP, 1, 32, var)
+        assert e.value.code == dw.DW_ERR_ARG
     lat.close()
 
 
@@ -197,7 +201,7 @@ def test_both_variants_low_precision(prec):
     lat.load_gauge(U)
     refs = {op: run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mfs) for op in STENCIL_OPS}
     ran = set()
-    for variant in range(7):
+    for variant in range(8):
         for spt in (1, 2, 3, 4):
             for op in STENCIL_OPS:
                 try:
@@ -207,7 +211,7 @@ def test_both_variants_low_precision(prec):
                 ran.add((variant, op))
                 got = run_gpu(lat, op, psi, mf=mfs)
                 assert max_rel(got, refs[op]) <= TOL[prec], (OP_NAMES[op], spt, variant)
-    built = tuple(range(6))  # variant 6 needs Lx = 32: its own test below
+    built = tuple(range(6))  # variants 6, 7 need Lx = 32: their own test below
     assert {(v, op) for v in built for op in STENCIL_OPS} <= ran
     lat.close()
 
@@ -330,7 +334,7 @@ def test_tune_picks_valid_tile_and_stays_exact():
         assert dims[2] % zblk == 0
         assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
         assert (Ls // spt) % sgrp == 0 and (sgrp == 1 or op != dw.DW_OP_DDAG)
-        assert variant in range(7)
+        assert variant in range(8)
         got = run_gpu(lat, op, psi, mf=[0.01])
         ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
         assert max_rel(got, ref) <= TOL[dw.DW_F32], OP_NAMES[op]
