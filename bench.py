@@ -262,20 +262,24 @@ BATCH_DIMS, BATCH_LS, BATCH_SEED = (16, 16, 16, 32), 12, 4
 BATCH_MASSES = [0.005] * 5 + [0.01] * 4 + [0.02] * 2 + [0.05]
 
 
-def bench_cg(args):
-    """CG on D^+D x = b to a true residual of 1e-10 at 24^4 x Ls=16, m_f = 0.01:
-    plain FP64 against mixed FP32 and mixed FP16-storage, wall time of the whole
-    dw_cg_solve call; every solution's residual is recomputed by the oracle."""
+def bench_cg(args, dims=None, Ls=None, seed=None):
+    """CG on D^+D x = b to a true residual of 1e-10 (default 24^4 x Ls=16, m_f =
+    0.01): plain FP64 against mixed FP32 and mixed FP16-storage, wall time of the
+    whole dw_cg_solve call; every solution's residual is recomputed by the oracle."""
     import oracle
     import torch
     from paper_2112_01852_gb300 import dw, inputs
     from paper_2112_01852_gb300.lattice import Lattice
-    U = inputs.exp_su3_field(CG_DIMS, seed=CG_SEED)
-    rhs = inputs.gaussian_fermion(CG_DIMS, CG_LS, 1, seed=CG_SEED)
-    lat = Lattice(CG_DIMS, CG_LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
+    dims = CG_DIMS if dims is None else dims
+    Ls = CG_LS if Ls is None else Ls
+    seed = CG_SEED if seed is None else seed
+    U = inputs.exp_su3_field(dims, seed=seed)
+    rhs = inputs.gaussian_fermion(dims, Ls, 1, seed=seed)
+    lat = Lattice(dims, Ls, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
     lat.load_gauge(U)
     bdev = lat.pack(rhs)
-    out = {"workload": "mobius_cg_24x24x24x24_ls16_mf0.01", "tol": 1e-10}
+    out = {"workload": "mobius_cg_%s_ls%d_mf%g" % ("x".join(str(d) for d in dims), Ls, MF),
+           "tol": 1e-10}
     for name, mode in (("f64", dw.DW_F64), ("mixed_f32", dw.DW_F32), ("mixed_f16", dw.DW_F16)):
         x = lat.empty(1)
         torch.cuda.synchronize()
@@ -285,7 +289,7 @@ def bench_cg(args):
         status, stats = lat.cg(x, bdev, [MF], nrhs=1, tol=1e-10, maxit=40000, mode=mode)
         wall = time.perf_counter() - t0
         xs = lat.unpack(x)
-        Ax = oracle.dwdagdw(xs, U, CG_DIMS, CG_LS, M5, B, C, [MF])
+        Ax = oracle.dwdagdw(xs, U, dims, Ls, M5, B, C, [MF])
         res = float(np.linalg.norm((rhs - Ax).ravel()) / np.linalg.norm(rhs.ravel()))
         out[name] = {"seconds": wall, "status": status, "iters": stats[0].iters,
                      "reliable_updates": stats[0].reliable_updates,
@@ -374,6 +378,8 @@ def main():
     ap.add_argument("--tile", default=None,
                     help="spt,tx[,variant[,zblk[,sgrp]]]: fixed Dhop tile instead of tuning")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--cg-full", action="store_true",
+                    help="also run the three CGs on the benchmark lattice (minutes)")
     args = ap.parse_args()
     global DIMS, LS
     if args.dims:
@@ -507,6 +513,22 @@ def main():
     del x16, y16
     lat16.close()
 
+    # Wilson Dslash: the same kernel at Ls = 1 on the same 4D lattice
+    latw = Lattice(DIMS, 1, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32)
+    latw.load_gauge(U)
+    psiw = inputs.gaussian_fermion(DIMS, 1, 1, seed=SEED)
+    xw = latw.pack(psiw)
+    yw = latw.empty(1)
+    tw = latw.tune(dw.DW_OP_DHOP, 1)
+    msw = time_op(lambda: dw.dw_apply_Dhop(latw.handle, yw.data_ptr(), xw.data_ptr(), 1, sh),
+                  args.steps, 3, stream)
+    ops_out["wilson_dslash_f32"] = {"ms": msw, "gflops": FLOP_DHOP * V4 / msw / 1e6,
+                                    "gbs": bytes_per_site(4, 1) * V4 / msw / 1e6,
+                                    "frac": bytes_per_site(4, 1) * V4 / msw / 1e6 / peak,
+                                    "tile": tw}
+    del xw, yw
+    latw.close()
+
     # end to end through the host-buffer entry point (pinned host, H2D + D2H inside)
     nbytes = lat.fermion_bytes(1)
     hin = x.cpu().pin_memory()
@@ -534,6 +556,8 @@ def main():
     if not args.no_cg:
         line["batched"] = bench_batched(args)
         line["cg"] = bench_cg(args)
+        if args.cg_full:
+            line["cg_full"] = bench_cg(args, DIMS, LS, SEED)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

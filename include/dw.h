@@ -185,6 +185,56 @@ int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int n
                 double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
 
 /*
+ * Even-odd (red-black) preconditioning.  Sites are even or odd by
+ * x + y + z + t; D = A + H with the local part A = alpha + beta K
+ * (alpha = b (4 - M5) + 1, beta = c (4 - M5) - 1) and the hopping part
+ * H = -Dhop (b + cK) / 2, which couples only opposite parities.  The Schur
+ * complement on odd sites is Dhat = A - H_oe A^-1 H_eo (its adjoint
+ * Dhat^+ = A^+ - H_eo^+ A^-+ H_oe^+), and D x = eta is equivalent to
+ * Dhat x_o = eta_o - H_oe A^-1 eta_e, x_e = A^-1 (eta_e - H_eo x_o).  The paper
+ * has no preconditioner; this is the standard construction.
+ *
+ * Single-parity fields ("eo fields") hold the V4/2 sites of one parity in the
+ * blocked layout over the checkerboard index x4/2 (x4 the lexicographic site
+ * index), V4/2 padded to a multiple of 32; dw_fermion_bytes_eo gives their
+ * size.  All of these need Lx, Ly, Lz and Lt even (with an odd extent the
+ * periodic hop across that edge joins sites of the same parity); DW_ERR_ARG
+ * otherwise (dw_fermion_bytes_eo returns 0).
+ *
+ * dw_eo_split / dw_eo_merge: copy a full internal-layout field at precision
+ * `prec` to its even and odd fields and back (device buffers, nrhs each).
+ * dw_apply_m5_eo: out = A in (inverse: A^-1 in; dag: A^+ / A^-+) on eo fields at
+ * the lattice precision, per-RHS masses mf[nrhs] (HOST).
+ * dw_apply_schur: out = Dhat in (dag: Dhat^+ in) on odd eo fields at the lattice
+ * precision; the even intermediates live in lattice scratch.  out must not
+ * alias in.  Stream-ordered, asynchronous.
+ */
+size_t dw_fermion_bytes_eo(const dw_lattice *lat, int prec, int nrhs);
+int dw_eo_split(dw_lattice *lat, void *even, void *odd, const void *full, int prec, int nrhs,
+                void *stream);
+int dw_eo_merge(dw_lattice *lat, void *full, const void *even, const void *odd, int prec,
+                int nrhs, void *stream);
+int dw_apply_m5_eo(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                   int inverse, int dag, void *stream);
+int dw_apply_schur(dw_lattice *lat, void *out, const void *in, const double *mf, int nrhs,
+                   int dag, void *stream);
+
+/*
+ * Solve D x = eta with even-odd preconditioning: CG (mode as in dw_cg_solve:
+ * FP64, or mixed FP32 / FP16 inner operator with FP64 reliable updates) on
+ * Dhat^+ Dhat x_o = Dhat^+ (eta_o - H_oe A^-1 eta_e), stopped when the FP64
+ * residual of that system is below tol relative to its right-hand side; then
+ * x_e = A^-1 (eta_e - H_eo x_o).  x (start vector: its odd sites) and eta are
+ * full DEVICE fields in the internal layout at DW_F64; mf[nrhs] HOST.  stats:
+ * iters and reliable_updates of the odd-site CG, converged for that CG,
+ * true_resid = |eta - D x| / |eta| recomputed in FP64 on the full lattice,
+ * seconds for the whole call.  Needs even extents.  Returns DW_OK,
+ * DW_ERR_NOT_CONVERGED or DW_ERR_BREAKDOWN.  Synchronises.
+ */
+int dw_solve_eo(dw_lattice *lat, void *x, const void *eta, const double *mf, int nrhs,
+                double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
+
+/*
  * Stencil-kernel tiles.  A tile is (spt, tx, variant, zblk, sgrp): spt fifth-dimension
  * slices per thread (1..4, dividing Ls), tx 4D sites per CTA (a multiple of
  * 32, taken from one (x, y) plane), the load variant of the hop phase (0 =

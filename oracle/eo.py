@@ -6,7 +6,8 @@ The paper gives no solver and no preconditioner; this is the standard Schur
 complement of the 4D even-odd split, written from the operator definition with
 the oracle's own Dhop and K (``oracle.dhop``, ``oracle.kop``) and numpy.
 
-Sites are even or odd by (x + y + z + t) mod 2.  The operator
+Sites are even or odd by (x + y + z + t) mod 2; every extent must be even
+(a periodic hop across an odd extent joins sites of equal parity).  The operator
     D = D_W (b + cK) + (1 - K),   D_W = (4 - M5) - Dhop / 2
 splits into a part that is local in 4D,
     A = (4 - M5)(b + cK) + (1 - K) = alpha + beta K,

@@ -159,6 +159,10 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.t_begin = t_begin;
     p.t_count = t_count;
     p.status = lat->dev_status;
+    p.own = p.in;
+    p.alpha = lat->b * (4.0 - lat->M5) + 1.0;
+    p.beta = lat->c * (4.0 - lat->M5) - 1.0;
+    p.hscale = -0.5;
     p.M5 = lat->M5;
     p.b = lat->b;
     p.c = lat->c;

@@ -48,4 +48,26 @@ int apply_host_pipelined(dw_lattice *lat, int op, void *out_host, const void *in
                          const double *mf, int nrhs, cudaStream_t st);
 void pipe_release(dw_lattice *lat);
 
+// Even-odd pieces (dw_eo.cu).  Single-parity fields: V4/2 sites, blocked.
+bool eo_ok(const dw_lattice *lat);  // every extent even
+size_t cb_field_bytes(const dw_lattice *lat, int prec, int nrhs);
+int eo_split(dw_lattice *lat, int prec, void *even, void *odd, const void *full, int nrhs,
+             cudaStream_t st);
+int eo_merge(dw_lattice *lat, int prec, void *full, const void *even, const void *odd, int nrhs,
+             cudaStream_t st);
+// out = A in, A^-1 in, A^+ in or A^-+ in (A = alpha + beta K), on parity fields
+int apply_m5(dw_lattice *lat, int prec, void *out, const void *in, const double *mf, int nrhs,
+             bool inv, bool dag, cudaStream_t st);
+// out (parity) = alpha own + beta K own + hscale Dhop (b + cK) nbr (OP_D), or the
+// D^+ form (OP_DDAG); own may be null
+int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr, const void *own,
+                  int parity, double alpha, double beta, double hscale, const double *mf,
+                  int nrhs, cudaStream_t st, const int *gate, int gate_stride,
+                  double *norm_partials);
+long long cb_ctas_per_rhs(const dw_lattice *lat, int prec, int op);
+// out_o = Dhat in_o or Dhat^+ in_o; t1, t2 even scratch fields
+int apply_schur(dw_lattice *lat, int prec, void *out, const void *in, const double *mf, int nrhs,
+                bool dag, void *t1, void *t2, cudaStream_t st, const int *gate, int gate_stride,
+                double *norm_partials);
+
 }  // namespace dw

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kBlasThreads)
                     double *partial, const CGState *st) {
   const int rhs = blockIdx.y;
   double s = 0.0;
-  if (st[rhs].need_update) {
+  if (!st || st[rhs].need_update) {  // null state: every RHS
     double *pr = RHS_PTR(double *, r, rhs, bytes);
     const double *pb = RHS_PTR(const double *, b, rhs, bytes);
     const double *pa = RHS_PTR(const double *, Ax, rhs, bytes);

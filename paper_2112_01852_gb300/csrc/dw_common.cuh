@@ -162,6 +162,10 @@ struct DslashParams {
   int t_begin;          // output sites: the time slices t_begin .. t_begin + t_count - 1
   int t_count;          // (0: all Lt; the inputs are read on the whole lattice)
   int *status;          // lattice-owned device word; set nonzero when a bounded wait gives up
+  const void *own;      // field of the local term of D / D^+ (null: hopping term alone)
+  int parity;           // checkerboard launches: parity of the output sites
+  double alpha, beta;   // local term alpha psi + beta K psi (K^+ for D^+)
+  double hscale;        // factor of the hopping term (-1/2 in D_W)
   double M5, b, c;
   double mf[64];         // per-RHS masses, passed by value
 };
@@ -196,6 +200,8 @@ inline size_t rows_smem_bytes(int tx, int nsl, int prec) {
 // that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA
 // launch error.
 int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
+// Checkerboard (single-parity) stencil, OP_D / OP_DDAG forms only.
+int launch_dslash_cb(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
 // Largest CTA the stencil kernel (op, spt, variant) can launch (0: none).
 int dslash_max_threads(int prec, int op, int spt, int variant);
 // Face halves of a t-decomposed sub-lattice (see dw_halo_pack).

@@ -901,7 +901,11 @@ struct RegCap {
 
 
 
-template <class P, int OP, int SPT, int VAR>
+// CB: the fields are single-parity (checkerboard) fields: a thread computes the
+// output site of parity p.parity with field index xf = x4 / 2 (x4 the full
+// lexicographic index; Lx even), its neighbours are read from the field of the
+// other parity at their x4 / 2, and the links stay full-lattice.
+template <class P, int OP, int SPT, int VAR, bool CB = false>
 __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   using C = typename P::C;
   using vec = typename P::vec;
@@ -919,7 +923,9 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   // planes instead of 2 Lz: the L2 then holds the reuse window.
   const int tx = blockDim.x;
   const int rhs = blockIdx.x % p.nrhs;
-  int x4, in_plane, sg;
+  const int Lxf = CB ? (p.L[0] >> 1) : p.L[0];  // field sites per x row
+  const int plane_sites = Lxf * p.L[1];
+  int x4, xf, in_plane, sg;  // full site, field index, index in the (x, y) plane
   {
     int id = blockIdx.x / p.nrhs;
     sg = id % p.sgrp;  // slice group: the CTAs of one tile are adjacent
@@ -931,13 +937,20 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     id /= bz;
     const int t = p.t_begin + id % p.t_count;
     const int zb = id / p.t_count;
+    const int z = zb * bz + zl;
     in_plane = tile * tx + threadIdx.x;
-    x4 = in_plane + p.L[0] * p.L[1] * ((zb * bz + zl) + p.L[2] * t);
+    xf = in_plane + plane_sites * (z + p.L[2] * t);
+    if (CB)
+      x4 = 2 * xf + (((in_plane / Lxf) + z + t + p.parity) & 1);
+    else
+      x4 = xf;
   }
+  // field index of a full neighbour index
+  auto fidx = [](int v) { return CB ? (v >> 1) : v; };
   const int chunk = threadIdx.y + sg * blockDim.y;  // slice group of this thread row
   const int nchunk = blockDim.y;                     // thread rows of the CTA
   if (p.gate && !p.gate[(long long)rhs * p.gate_stride]) return;  // whole CTA: uniform
-  const bool active = in_plane < p.L[0] * p.L[1];
+  const bool active = in_plane < plane_sites;
   const int s0 = chunk * SPT;
   const int Ls = p.Ls;
 
@@ -950,8 +963,13 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
 
   const C mf = (OP == OP_D || OP == OP_DDAG) ? (C)p.mf[rhs] : C(0);
   const C b = (C)p.b, c = (C)p.c;
-  const C alpha = (C)(p.b * (4.0 - p.M5) + 1.0);
-  const C beta = (C)(p.c * (4.0 - p.M5) - 1.0);
+  const C alpha = (C)p.alpha, beta = (C)p.beta;
+  // the field of the local term alpha psi + beta K psi (none: hopping term alone)
+  Field<P> Fo;
+  Fo.base = p.own ? reinterpret_cast<const vec *>(p.own) + (long long)rhs * p.rhs_stride
+                  : F.base;
+  Fo.V4 = p.V4;
+  Fo.Ls = p.Ls;
 
   Spinor<V2> acc[SPT];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1096,22 +1114,22 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       const int ct = x4 / Vf;
       const long long hplane = (long long)Ls * Vf;
       const long long hrhs = hplane * (12 / P::R);
-      if (p.halo_up && ct == p.L[3] - 1)
+      if (!CB && p.halo_up && ct == p.L[3] - 1)
         halo_hop_up<P, SF, true, SPT>(acc, (const vec *)p.halo_up + rhs * hrhs, hplane, Vf,
                                       x4 - ct * Vf, gauge, x4, (C)H.sign<3, true>(p), s0);
       else
         hop_dir<P, 3, SF, false, PHI, true, SPT, VAR >= 4 ? HINT_KEEP : HINT_NONE>(
-            acc, F, gauge, (C)H.sign<3, true>(p), H.nb<3, true>(p), x4, s0, Ls, b, c, mf);
-      if (p.halo_dn && ct == 0)
+            acc, F, gauge, (C)H.sign<3, true>(p), fidx(H.nb<3, true>(p)), x4, s0, Ls, b, c, mf);
+      if (!CB && p.halo_dn && ct == 0)
         halo_hop_down<P, SB, SPT>(acc, (const vec *)p.halo_dn + rhs * hrhs, hplane, Vf, x4, s0);
       else
         hop_dir<P, 3, SB, true, PHI, false, SPT, VAR >= 4 ? HINT_DROP : HINT_NONE>(
-            acc, F, gauge, (C)H.sign<3, false>(p), H.nb<3, false>(p), H.nb<3, false>(p), s0, Ls,
-            b, c, mf);
+            acc, F, gauge, (C)H.sign<3, false>(p), fidx(H.nb<3, false>(p)), H.nb<3, false>(p),
+            s0, Ls, b, c, mf);
 #define DW_HOP(MU, FWD, S, ADJ)                                                                  \
   hop_dir<P, MU, S, ADJ, PHI, false, SPT>(acc, F, gauge, (C)H.sign<MU, FWD>(p),                \
-                                          H.nb<MU, FWD>(p), FWD ? x4 : H.nb<MU, FWD>(p), s0,    \
-                                          Ls, b, c, mf)
+                                          fidx(H.nb<MU, FWD>(p)), FWD ? x4 : H.nb<MU, FWD>(p), \
+                                          s0, Ls, b, c, mf)
       DW_HOP(2, true, SF, false);
       DW_HOP(2, false, SB, true);
       DW_HOP(1, true, SF, false);
@@ -1145,9 +1163,9 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   }
 
   auto store = [&](int j, const Spinor<V2> &v) {
-    store_spinor<P>(out + F.site(s0 + j, x4), kPlaneStride, v);
+    store_spinor<P>(out + F.site(s0 + j, xf), kPlaneStride, v);
   };
-  const V2 mhalf = bc<V2>(C(-0.5));
+  const V2 mhalf = bc<V2>((C)p.hscale);  // -1/2 of D_W, or the caller's factor
 
   if (OP == OP_DHOP || OP == OP_DHOP_DAG) {
     if (active) {
@@ -1158,8 +1176,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     // out = alpha psi + beta K psi - 1/2 Dhop phi; optionally |out|^2 per CTA
     // (the CG's <p, D^+D p> = |D p|^2, fused here to save a pass over two fields)
     double nsq = 0.0;
-    if (active) {
-      roll_5d<P, false, SPT>(F, x4, s0, Ls, alpha, beta, mf, [&](int j, const Spinor<V2> &v) {
+    auto emit = [&](int j, const Spinor<V2> &v) {
         Spinor<V2> o;
         C ss = 0;
 #pragma unroll
@@ -1177,7 +1194,19 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         }
         nsq += (double)ss;
         store(j, o);
-      });
+    };
+    if (active) {
+      if (p.own) {
+        roll_5d<P, false, SPT>(Fo, xf, s0, Ls, alpha, beta, mf, emit);
+      } else {
+        Spinor<V2> zero_v;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          zero_v.up.re[cc] = zero_v.up.im[cc] = zero_v.lo.re[cc] = zero_v.lo.im[cc] = bc<V2>(C(0));
+        }
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) emit(j, zero_v);
+      }
     }
     if (p.norm_partials) {
       // fixed-order block sum: warp shuffles, then warp 0 over the warp sums
@@ -1218,8 +1247,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       const int cp = (chunk == 0) ? nchunk - 1 : chunk - 1;
       const V2 fn = bc<V2>((chunk + 1 == nchunk) ? -mf : C(1));
       const V2 fp = bc<V2>((chunk == 0) ? -mf : C(1));
-      const V2 mb = bc<V2>(C(-0.5) * b), mc = bc<V2>(C(-0.5) * c);
-      roll_5d<P, true, SPT>(F, x4, s0, Ls, alpha, beta, mf, [&](int j, const Spinor<V2> &v) {
+      const V2 mb = bc<V2>((C)p.hscale * b), mc = bc<V2>((C)p.hscale * c);
+      auto emit = [&](int j, const Spinor<V2> &v) {
         Spinor<V2> o;
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
@@ -1245,28 +1274,39 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
           o.lo.im[cc] = p_fma(mc, kli, p_fma(mb, acc[j].lo.im[cc], v.lo.im[cc]));
         }
         store(j, o);
-      });
+      };
+      if (p.own) {
+        roll_5d<P, true, SPT>(Fo, xf, s0, Ls, alpha, beta, mf, emit);
+      } else {
+        Spinor<V2> zero_v;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          zero_v.up.re[cc] = zero_v.up.im[cc] = zero_v.lo.re[cc] = zero_v.lo.im[cc] = bc<V2>(C(0));
+        }
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) emit(j, zero_v);
+      }
     }
   }
 }
 
-template <class P, int OP, int SPT, int VAR>
+template <class P, int OP, int SPT, int VAR, bool CB>
 __global__ void dslash_kernel(const DslashParams p) {
-  dslash_body<P, OP, SPT, VAR>(p);
+  dslash_body<P, OP, SPT, VAR, CB>(p);
 }
 
-template <class P, int OP, int SPT, int VAR>
+template <class P, int OP, int SPT, int VAR, bool CB>
 __global__ void __maxnreg__(RegCap<VAR>::value) dslash_kernel_capped(const DslashParams p) {
-  dslash_body<P, OP, SPT, VAR>(p);
+  dslash_body<P, OP, SPT, VAR, CB>(p);
 }
 
-// The kernel entry of (P, OP, SPT, VAR): variant 4 is register capped.
-template <class P, int OP, int SPT, int VAR>
+// The kernel entry of (P, OP, SPT, VAR, CB): variants 4, 6, 7 are register capped.
+template <class P, int OP, int SPT, int VAR, bool CB = false>
 constexpr void (*dslash_entry())(const DslashParams) {
   if constexpr (RegCap<VAR>::value > 0)
-    return dslash_kernel_capped<P, OP, SPT, VAR>;
+    return dslash_kernel_capped<P, OP, SPT, VAR, CB>;
   else
-    return dslash_kernel<P, OP, SPT, VAR>;
+    return dslash_kernel<P, OP, SPT, VAR, CB>;
 }
 
 template <class P, int OP, int SPT, int VAR>
@@ -1278,15 +1318,19 @@ size_t dslash_smem(int tx, int nchunk) {
   return smem;
 }
 
-template <class P, int OP, int SPT, int VAR>
+template <class P, int OP, int SPT, int VAR, bool CB = false>
 int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t st) {
   // D^+ exchanges slice-group edges through shared memory: one CTA per tile
   if (sgrp < 1 || (p.Ls / SPT) % sgrp || (OP == OP_DDAG && sgrp != 1)) return -2;
+  // checkerboard launches: register variants only, Lx even, no halos
+  if (CB && ((VAR != 0 && VAR != 4 && VAR != 5) || (p.L[0] & 1) || p.halo_up || p.halo_dn))
+    return -2;
   const int nchunk = p.Ls / SPT / sgrp;
   dim3 block(tx, nchunk);
   DslashParams q = p;
+  const int plane_sites = (CB ? p.L[0] / 2 : p.L[0]) * p.L[1];
   // variant 7: one CTA per plane (it walks the plane's tiles itself)
-  q.tiles_per_plane = VAR == 7 ? 1 : (p.L[0] * p.L[1] + tx - 1) / tx;
+  q.tiles_per_plane = VAR == 7 ? 1 : (plane_sites + tx - 1) / tx;
   q.zblk = zblk;
   q.sgrp = sgrp;
   if (zblk < 1 || p.L[2] % zblk) return -2;
@@ -1305,29 +1349,30 @@ int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t s
   static size_t smem_set = 48 * 1024;
   if (!max_threads) {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dslash_entry<P, OP, SPT, VAR>()) != cudaSuccess) return -1;
+    if (cudaFuncGetAttributes(&fa, dslash_entry<P, OP, SPT, VAR, CB>()) != cudaSuccess)
+      return -1;
     max_threads = fa.maxThreadsPerBlock;
   }
   if (tx < 32 || tx % 32 || tx * nchunk > max_threads) return -3;
   if (smem > 227 * 1024) return -3;
   if (smem > smem_set) {
-    if (cudaFuncSetAttribute(dslash_entry<P, OP, SPT, VAR>(),
+    if (cudaFuncSetAttribute(dslash_entry<P, OP, SPT, VAR, CB>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return -3;
     smem_set = smem;
   }
-  dslash_entry<P, OP, SPT, VAR>()<<<grid, block, smem, st>>>(q);
+  dslash_entry<P, OP, SPT, VAR, CB>()<<<grid, block, smem, st>>>(q);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <class P, int OP, int VAR>
+template <class P, int OP, int VAR, bool CB = false>
 int launch_spt(const DslashParams &p, TileConfig cfg, cudaStream_t st) {
   switch (cfg.spt) {
-    case 1: return launch_one<P, OP, 1, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
-    case 2: return launch_one<P, OP, 2, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
-    case 3: return launch_one<P, OP, 3, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
-    case 4: return launch_one<P, OP, 4, VAR>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
+    case 1: return launch_one<P, OP, 1, VAR, CB>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
+    case 2: return launch_one<P, OP, 2, VAR, CB>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
+    case 3: return launch_one<P, OP, 3, VAR, CB>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
+    case 4: return launch_one<P, OP, 4, VAR, CB>(p, cfg.tx, cfg.zblk, cfg.sgrp, st);
     default: return -2;
   }
 }
@@ -1381,6 +1426,18 @@ int launch_variant(const DslashParams &p, int op, TileConfig cfg, cudaStream_t s
   return -2;
 }
 
+// Checkerboard entry points (the D and D^+ forms; Dhop is D with b = 1,
+// c = 0, no local term and factor 1).
+template <class P, int VAR>
+int launch_variant_cb(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st) {
+  if (cfg.spt < 1 || p.Ls % cfg.spt) return -2;
+  switch (op) {
+    case OP_D: return launch_spt<P, OP_D, VAR, true>(p, cfg, st);
+    case OP_DDAG: return launch_spt<P, OP_DDAG, VAR, true>(p, cfg, st);
+  }
+  return -2;
+}
+
 template <class P, int VAR>
 int max_threads_variant(int op, int spt) {
   switch (op) {
@@ -1403,6 +1460,15 @@ int max_threads_variant(int op, int spt) {
   }                                                                                      \
   int dslash_max_threads_##PREC##_v##VAR(int op, int spt) {                              \
     return max_threads_variant<PREC, VAR>(op, spt);                                      \
+  }                                                                                      \
+  }
+
+// Checkerboard stencil of one (precision, variant).
+#define DW_DSLASH_CB_INSTANTIATE(PREC, VAR)                                               \
+  namespace dw {                                                                         \
+  int launch_dslash_cb_##PREC(const DslashParams &p, int op, TileConfig cfg,             \
+                              cudaStream_t st) {                                         \
+    return launch_variant_cb<PREC, VAR>(p, op, cfg, st);                                 \
   }                                                                                      \
   }
 

@@ -42,6 +42,19 @@ int dslash_max_threads_F16_v6(int op, int spt);
 int launch_dslash_F16_v7(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v7(int op, int spt);
 
+int launch_dslash_cb_F64(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int launch_dslash_cb_F32(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int launch_dslash_cb_F16(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+
+int launch_dslash_cb(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st) {
+  switch (prec) {
+    case DW_F64: return launch_dslash_cb_F64(p, op, cfg, st);
+    case DW_F32: return launch_dslash_cb_F32(p, op, cfg, st);
+    case DW_F16: return launch_dslash_cb_F16(p, op, cfg, st);
+  }
+  return -2;
+}
+
 int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st) {
   const int cfg_variant = cfg.variant;
   switch (prec) {

@@ -54,7 +54,8 @@ SYMBOLS = (
     "dw_apply_DdagD_noalloc", "dw_apply_host",
     "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_device_status", "dw_halo_bytes",
     "dw_halo_pack", "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
-    "dw_unpack_fermion", "dw_last_error",
+    "dw_unpack_fermion", "dw_last_error", "dw_fermion_bytes_eo", "dw_eo_split", "dw_eo_merge",
+    "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo",
 )
 
 
@@ -107,6 +108,12 @@ def load_library():
             "dw_set_tile": (I, [P, I, I, I, I, I, I, I, I]),
             "dw_tune": (I, [P, I, I, IP, IP, IP, IP, IP, P]),
             "dw_device_status": (I, [P]),
+            "dw_fermion_bytes_eo": (S, [P, I, I]),
+            "dw_eo_split": (I, [P, P, P, P, I, I, P]),
+            "dw_eo_merge": (I, [P, P, P, P, I, I, P]),
+            "dw_apply_m5_eo": (I, [P, P, P, DP, I, I, I, P]),
+            "dw_apply_schur": (I, [P, P, P, DP, I, I, P]),
+            "dw_solve_eo": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
             "dw_halo_bytes": (S, [P, I, I]),
             "dw_halo_pack": (I, [P, P, P, P, I, I, P]),
             "dw_apply_Dhop_halo": (I, [P, P, P, P, P, I, I, P]),
@@ -202,6 +209,15 @@ def dw_cg_solve(lat, x, b, mf, nrhs, tol, maxit, mode, stream=0):
     return rc, list(stats)
 
 
+def dw_solve_eo(lat, x, eta, mf, nrhs, tol, maxit, mode, stream=0):
+    """D x = eta with even-odd preconditioning; returns (status, [dw_cg_stats]*nrhs)."""
+    stats = (dw_cg_stats * int(nrhs))()
+    rc = _check(load_library().dw_solve_eo(lat, x, eta, _doubles(mf), int(nrhs), float(tol),
+                                           int(maxit), int(mode), stats, stream),
+                allow=(DW_ERR_NOT_CONVERGED,))
+    return rc, list(stats)
+
+
 def dw_set_tile(lat, op, prec, nrhs, spt, tx, variant=0, zblk=0, sgrp=1):
     _check(load_library().dw_set_tile(lat, int(op), int(prec), int(nrhs), int(spt), int(tx),
                                       int(variant), int(zblk), int(sgrp)))
@@ -218,6 +234,28 @@ def dw_tune(lat, op, nrhs, stream=0):
 def dw_device_status(lat):
     """Raises DWError (DW_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
     _check(load_library().dw_device_status(lat))
+
+
+def dw_fermion_bytes_eo(lat, prec, nrhs):
+    return int(load_library().dw_fermion_bytes_eo(lat, int(prec), int(nrhs)))
+
+
+def dw_eo_split(lat, even, odd, full, prec, nrhs, stream=0):
+    _check(load_library().dw_eo_split(lat, even, odd, full, int(prec), int(nrhs), stream))
+
+
+def dw_eo_merge(lat, full, even, odd, prec, nrhs, stream=0):
+    _check(load_library().dw_eo_merge(lat, full, even, odd, int(prec), int(nrhs), stream))
+
+
+def dw_apply_m5_eo(lat, out, inp, mf, nrhs, inverse, dag, stream=0):
+    _check(load_library().dw_apply_m5_eo(lat, out, inp, _doubles(mf), int(nrhs), int(inverse),
+                                         int(dag), stream))
+
+
+def dw_apply_schur(lat, out, inp, mf, nrhs, dag, stream=0):
+    _check(load_library().dw_apply_schur(lat, out, inp, _doubles(mf), int(nrhs), int(dag),
+                                         stream))
 
 
 def dw_halo_bytes(lat, prec, nrhs):

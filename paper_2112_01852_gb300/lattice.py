@@ -57,6 +57,29 @@ class Lattice:
         n = self.fermion_bytes(nrhs, prec)
         return torch.empty(n, dtype=torch.uint8, device="cuda")
 
+    def empty_eo(self, nrhs=1, prec=None):
+        """A single-parity field (V4/2 sites; needs all four extents even)."""
+        n = dw.dw_fermion_bytes_eo(self.handle, self.prec if prec is None else prec, nrhs)
+        return torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def pack_eo(self, psi, prec=None):
+        """Canonical complex128 numpy (nrhs, V4, Ls, 4, 3) -> (even, odd) device fields."""
+        prec = self.prec if prec is None else prec
+        full = self.pack(psi, prec)
+        nrhs = 1 if np.ndim(psi) == 4 else np.shape(psi)[0]
+        even, odd = self.empty_eo(nrhs, prec), self.empty_eo(nrhs, prec)
+        dw.dw_eo_split(self.handle, even.data_ptr(), odd.data_ptr(), full.data_ptr(), prec, nrhs,
+                       _stream())
+        return even, odd
+
+    def unpack_eo(self, even, odd, nrhs=1, prec=None):
+        """(even, odd) device fields -> canonical complex128 numpy (nrhs, V4, Ls, 4, 3)."""
+        prec = self.prec if prec is None else prec
+        full = self.empty(nrhs, prec)
+        dw.dw_eo_merge(self.handle, full.data_ptr(), even.data_ptr(), odd.data_ptr(), prec, nrhs,
+                       _stream())
+        return self.unpack(full, nrhs, prec)
+
     def load_gauge(self, U):
         """U: complex128 numpy (V4, 4, 3, 3), canonical layout."""
         U = np.ascontiguousarray(U, dtype=np.complex128)
@@ -115,6 +138,11 @@ class Lattice:
 
     def tune(self, op, nrhs=1):
         return dw.dw_tune(self.handle, op, nrhs, _stream())
+
+    def solve_eo(self, x, eta, mf, nrhs=1, tol=1e-10, maxit=10000, mode=dw.DW_F32):
+        """D x = eta by even-odd preconditioned CG (FP64 full fields)."""
+        return dw.dw_solve_eo(self.handle, x.data_ptr(), eta.data_ptr(), _masses(mf, nrhs), nrhs,
+                              tol, maxit, mode, _stream())
 
     def cg(self, x, b, mf, nrhs=1, tol=1e-10, maxit=10000, mode=dw.DW_F32):
         return dw.dw_cg_solve(self.handle, x.data_ptr(), b.data_ptr(), _masses(mf, nrhs), nrhs,
