@@ -9,7 +9,11 @@ Prints one JSON line: throughput in GFlop/s (1320-flop convention), the HBM
 roofline of the kernel against the measured copy bandwidth, an end-to-end
 figure through the host-buffer C entry point, the CPU oracle as a baseline,
 and the SM clocks sampled during the timed region.  The fused D, D^+ and
-D^+D applies and the FP16-storage Dhop are timed too and reported under "ops".
+D^+D applies, the FP16-storage Dhop and the Wilson Dslash (the same kernel at
+Ls = 1) are timed too and reported under "ops"; "batched" is the 12-RHS
+workload at 16^3 x 32 x 12, "cg" the FP64 / mixed CG on D^+D at 24^4 x 16 and
+"cg_eo" the even-odd preconditioned solve of D x = eta on the same lattice
+(--no-cg skips those; --cg-full adds the CGs on the benchmark lattice).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -302,6 +306,54 @@ def bench_cg(args, dims=None, Ls=None, seed=None):
     return out
 
 
+def bench_eo(args):
+    """D x = eta at 24^4 x Ls=16, m_f = 0.01, to 1e-10: even-odd preconditioned CG
+    (FP64 and mixed FP32 / FP16) against plain mixed-FP32 CG on D^+D x = D^+ eta;
+    every solution's residual |eta - D x| / |eta| is recomputed by the oracle."""
+    import oracle
+    import torch
+    from paper_2112_01852_gb300 import dw, inputs
+    from paper_2112_01852_gb300.lattice import Lattice
+    U = inputs.exp_su3_field(CG_DIMS, seed=CG_SEED)
+    eta = inputs.gaussian_fermion(CG_DIMS, CG_LS, 1, seed=CG_SEED)
+    lat = Lattice(CG_DIMS, CG_LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
+    lat.load_gauge(U)
+    e = lat.pack(eta)
+    out = {"workload": "mobius_solve_D_%s_ls%d_mf%g" % ("x".join(str(d) for d in CG_DIMS),
+                                                         CG_LS, MF), "tol": 1e-10}
+
+    def resid(x):
+        r = oracle.dw(lat.unpack(x), U, CG_DIMS, CG_LS, M5, B, C, [MF]) - eta
+        return float(np.linalg.norm(r.ravel()) / np.linalg.norm(eta.ravel()))
+
+    for name, mode in (("eo_f64", dw.DW_F64), ("eo_mixed_f32", dw.DW_F32),
+                       ("eo_mixed_f16", dw.DW_F16)):
+        x = lat.empty(1)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status, stats = lat.solve_eo(x, e, [MF], nrhs=1, tol=1e-10, maxit=40000, mode=mode)
+        wall = time.perf_counter() - t0
+        out[name] = {"seconds": wall, "status": status, "iters": stats[0].iters,
+                     "reliable_updates": stats[0].reliable_updates,
+                     "true_resid": stats[0].true_resid, "oracle_resid": resid(x)}
+        del x
+    # the same system without preconditioning: CG on D^+D x = D^+ eta
+    b = lat.empty(1)
+    dw.dw_apply_Ddag(lat.handle, b.data_ptr(), e.data_ptr(), [MF], 1)
+    y = lat.empty(1)
+    y.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status, stats = lat.cg(y, b, [MF], nrhs=1, tol=1e-10, maxit=40000, mode=dw.DW_F32)
+    wall = time.perf_counter() - t0
+    out["unprec_mixed_f32"] = {"seconds": wall, "status": status, "iters": stats[0].iters,
+                               "oracle_resid": resid(y)}
+    out["speedup_eo_vs_unprec_mixed_f32"] = wall / out["eo_mixed_f32"]["seconds"]
+    lat.close()
+    return out
+
+
 def bench_batched(args):
     """12 right-hand sides over 4 masses (5/4/2/1) at 16^3 x 32 x Ls=12, FP32:
     one batched Dhop / D^+D launch per step, and one batched mixed-FP32 CG solve
@@ -556,6 +608,7 @@ def main():
     if not args.no_cg:
         line["batched"] = bench_batched(args)
         line["cg"] = bench_cg(args)
+        line["cg_eo"] = bench_eo(args)
         if args.cg_full:
             line["cg_full"] = bench_cg(args, DIMS, LS, SEED)
     if rank == 0:

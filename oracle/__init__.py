@@ -8,7 +8,9 @@ nothing from it.
 ``dw_oracle.cpp`` is a plain C++ implementation written from the operator's
 definition (4x4 spin matrices, 3x3 colour matrices, std::complex<double>);
 ``dense.py`` builds the same operators as explicit dense matrices with numpy
-for small lattices. Both follow the standard domain-wall operator, which the
+for small lattices; ``eo.py`` writes the even-odd Schur complement and its
+solve out of this package's Dhop and K with numpy. All follow the standard
+domain-wall operator, which the
 paper names (the "Domain Wall kernel", Sec. 4.1; its per-site work and flop
 count, Table 3) without writing it down.
 
