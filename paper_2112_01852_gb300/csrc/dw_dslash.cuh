@@ -486,6 +486,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// L2 prefetch of a contiguous global range (16-byte aligned, size a multiple of
+// 16); a hint, nothing waits for it.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+}
 // Wait for phase `parity` of the barrier; false after about a second or 2^24
 // polls, whichever comes first.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
@@ -1022,7 +1027,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     // Variant 6: one tile per CTA.  Variant 7: the CTA walks the Ly/R tiles of
     // its plane in y, keeping the rows in a ring of R + 2 slots (row v in slot
     // (v + 1) mod (R + 2)): each step copies only its R new rows, the two rows
-    // shared with the previous tile stay.
+    // shared with the previous tile stay, and the next step's t+ rows are
+    // prefetched into L2.
     constexpr bool RING = (VAR == 7);
     constexpr int NPV = 24 / P::R;
     const int nsl = nchunk * SPT;  // slices of this CTA
@@ -1059,6 +1065,18 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
           const int slot = RING ? (v + 1) % NR : r;
           const vec *src = F.base + ((long long)(plane_blk + y) * Ls + sbase) * NPV * 32;
           bulk_g2s(rows + (size_t)slot * row_vecs, src, row_bytes, bar);
+        }
+        if (RING && k + 1 < steps) {
+          // the t+ neighbours are the first touch of their plane (read from
+          // HBM): fetch the next step's into L2 while this step runs
+          const int LyLz = Ly * p.L[2];
+          const int tc = plane_blk / LyLz;
+          const int tp_blk = plane_blk + (tc == p.L[3] - 1 ? -(p.L[3] - 1) : 1) * LyLz;
+          for (int r = 0; r < R; ++r) {
+            const int y = (k + 1) * R + r;
+            bulk_prefetch_l2(F.base + ((long long)(tp_blk + y) * Ls + sbase) * NPV * 32,
+                             row_bytes);
+          }
         }
       }
       const Hops H(p, xs);
