@@ -272,6 +272,12 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
                 int zblk, int sgrp);
 int dw_tune(dw_lattice *lat, int op, int nrhs, int *spt, int *tx, int *variant, int *zblk,
             int *sgrp, void *stream);
+/*
+ * The tile that launches of (op, prec, nrhs) use now: the pinned or tuned one,
+ * else the untuned default.  Outputs may be NULL.
+ */
+int dw_get_tile(dw_lattice *lat, int op, int prec, int nrhs, int *spt, int *tx, int *variant,
+                int *zblk, int *sgrp);
 
 /*
  * Device-side status of the lattice's kernels.  Kernels that wait for their own

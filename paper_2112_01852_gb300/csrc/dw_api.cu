@@ -414,6 +414,22 @@ int dw_device_status(dw_lattice *lat) {
   return DW_OK;
 }
 
+int dw_get_tile(dw_lattice *lat, int op, int prec, int nrhs, int *spt, int *tx, int *variant,
+                int *zblk, int *sgrp) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
+  if (prec < DW_F64 || prec > DW_F16) return fail(DW_ERR_ARG, "unknown precision %d", prec);
+  if (nrhs < 0) return fail(DW_ERR_ARG, "nrhs must be >= 0");
+  const TileConfig t = pick_tile(lat, prec, op, nrhs);
+  if (spt) *spt = t.spt;
+  if (tx) *tx = t.tx;
+  if (variant) *variant = t.variant;
+  if (zblk) *zblk = t.zblk;
+  if (sgrp) *sgrp = t.sgrp;
+  return DW_OK;
+}
+
 size_t dw_halo_bytes(const dw_lattice *lat, int prec, int nrhs) {
   if (!lat || nrhs < 0 || prec < DW_F64 || prec > DW_F16) return 0;
   return halo_bytes(lat, prec, nrhs);

@@ -17,7 +17,7 @@ int auto_zblk(const dw_lattice *lat, int prec);
 TileConfig pick_tile(dw_lattice *lat, int prec, int op, int nrhs);
 bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t);
 // Time the valid tiles for (op, nrhs) at precision `prec` and store the best
-// (quick: only tx <= 64 and the automatic z-blocking).
+// (quick: only tx <= 128 and the automatic z-blocking).
 int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool quick = false);
 // Stencil launch (op = OpKind) at precision `prec` over nrhs RHS; mf_host may be
 // NULL for the hopping-only kinds; `force` overrides the tile choice.

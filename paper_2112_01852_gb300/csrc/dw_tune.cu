@@ -24,15 +24,20 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
   float best = 1e30f;
   TileConfig best_t = default_tile(lat, prec, op, nrhs);
   const int reps = 5;
+  // z-blockings: unblocked, the automatic one and twice that (quick: automatic)
   const int za = auto_zblk(lat, prec);
+  std::vector<int> zbs{za};
+  if (!quick) {
+    if (za != 1) zbs.push_back(1);
+    if (lat->dims[2] % (2 * za) == 0) zbs.push_back(2 * za);
+  }
   for (int variant = 0; variant < kNumVariants; ++variant)
     for (int spt : {1, 2, 3, 4})
       for (int tx : {32, 64, 128, 256})
-        for (int zblk : {1, 2, 4})
+        for (int zblk : zbs)
           for (int sgrp : {1, 2, 3, 4, 6}) {
             TileConfig t{spt, tx, variant, zblk, sgrp};
-            if (zblk != 1 && zblk != za) continue;  // unblocked and the automatic blocking
-            if (quick && (tx > 64 || zblk != za || sgrp > 2)) continue;
+            if (quick && tx > 128) continue;
             if (!tile_valid(lat, prec, op, t)) continue;
             // warm-up launch doubles as the validity check
             if (run_dslash(lat, prec, op, lat->stage_out, lat->stage_in, mf.data(), nrhs, st, &t)) {

@@ -55,7 +55,7 @@ SYMBOLS = (
     "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_device_status", "dw_halo_bytes",
     "dw_halo_pack", "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
     "dw_unpack_fermion", "dw_last_error", "dw_fermion_bytes_eo", "dw_eo_split", "dw_eo_merge",
-    "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo",
+    "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo", "dw_get_tile",
 )
 
 
@@ -107,6 +107,7 @@ def load_library():
             "dw_cg_solve": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
             "dw_set_tile": (I, [P, I, I, I, I, I, I, I, I]),
             "dw_tune": (I, [P, I, I, IP, IP, IP, IP, IP, P]),
+            "dw_get_tile": (I, [P, I, I, I, IP, IP, IP, IP, IP]),
             "dw_device_status": (I, [P]),
             "dw_fermion_bytes_eo": (S, [P, I, I]),
             "dw_eo_split": (I, [P, P, P, P, I, I, P]),
@@ -256,6 +257,14 @@ def dw_apply_m5_eo(lat, out, inp, mf, nrhs, inverse, dag, stream=0):
 def dw_apply_schur(lat, out, inp, mf, nrhs, dag, stream=0):
     _check(load_library().dw_apply_schur(lat, out, inp, _doubles(mf), int(nrhs), int(dag),
                                          stream))
+
+
+def dw_get_tile(lat, op, prec, nrhs):
+    """The (spt, tx, variant, zblk, sgrp) that launches of (op, prec, nrhs) use."""
+    vals = [ctypes.c_int() for _ in range(5)]
+    _check(load_library().dw_get_tile(lat, int(op), int(prec), int(nrhs),
+                                      *[ctypes.byref(v) for v in vals]))
+    return tuple(v.value for v in vals)
 
 
 def dw_halo_bytes(lat, prec, nrhs):

@@ -153,3 +153,23 @@ def test_cg_argument_errors():
         lat.cg(b, b, [0.01])
     assert e.value.code == dw.DW_ERR_ARG
     lat.close()
+
+
+def test_cg_tunes_its_inner_operator():
+    # the solver times tiles for its inner operator; every z-blocking it may
+    # choose must divide Lz (24 here: the automatic blocking is 3, which is
+    # neither 1, 2 nor 4)
+    from paper_2112_01852_gb300.lattice import Lattice
+    dims, Ls = (8, 8, 24, 4), 8
+    U, b = make_case(dims, Ls, 1, seed=71)
+    lat = Lattice(dims, Ls, kind=dw.DW_MOBIUS, M5=1.8, b=1.5, c=0.5, prec=dw.DW_F64)
+    lat.load_gauge(U)
+    bd = lat.pack(b)
+    x = lat.empty(1)
+    x.zero_()
+    lat.cg(x, bd, [0.1], nrhs=1, tol=1e-8, maxit=50, mode=dw.DW_F32)
+    for op in (dw.DW_OP_D, dw.DW_OP_DDAG):
+        spt, tx, variant, zblk, sgrp = dw.dw_get_tile(lat.handle, op, dw.DW_F32, 1)
+        assert Ls % spt == 0 and tx % 32 == 0 and dims[2] % zblk == 0
+        assert (Ls // spt) % sgrp == 0 and (op == dw.DW_OP_D or sgrp == 1)
+    lat.close()
