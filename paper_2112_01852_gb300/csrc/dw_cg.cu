@@ -221,11 +221,13 @@ int cg_run(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs, 
   // tile choice for the inner operator of this solve (timed once per lattice
   // and RHS count, then cached; the FP64 operator of the reliable updates keeps
   // the untuned tile unless it is the inner operator)
-  if (!eo)
-    for (int op : {(int)OP_D, (int)OP_DDAG})
-      if (!lat->tuned.count(std::make_tuple(S.pp, op, nrhs)) &&
-          (rc = tune_tile(lat, S.pp, op, nrhs, st, true)))
-        return rc;
+  for (int op : {(int)OP_D, (int)OP_DDAG}) {
+    if (eo)
+      rc = tune_cb(lat, S.pp, op, st);
+    else if (!lat->tuned.count(std::make_tuple(S.pp, op, nrhs)))
+      rc = tune_tile(lat, S.pp, op, nrhs, st, true);
+    if (rc) return rc;
+  }
 
   {
     const long long nd = S.ctas_d();

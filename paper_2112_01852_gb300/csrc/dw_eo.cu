@@ -16,6 +16,7 @@
 // stencil kernel in its checkerboard form; A, A^-1 and their adjoints are a
 // separate kernel that walks the fifth dimension of one (site, spin half,
 // colour) per thread.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -198,9 +199,13 @@ int launch_m5_p(const M5Params &q, bool inv, cudaStream_t st) {
 }
 
 // Tile of the checkerboard stencil: two slices per thread where Ls allows,
-// 32-site tiles, the register variant (capped at FP32 / FP16), slice groups of
-// four slices for D (D^+ keeps all slices in one CTA).
-TileConfig cb_tile(const dw_lattice *lat, int prec, int op) {
+// 32-site tiles, the register variant (capped at FP32 / FP16), and for D at
+// FP32 / FP16 the slice groups split over three (else two) CTAs, as the tuner
+// prefers on the full lattice (D^+ keeps all slices in one CTA).
+// Key of a tuned checkerboard tile in the lattice's tile map (its own op codes).
+constexpr int kCbOpKey = 16;
+
+TileConfig cb_default_tile(const dw_lattice *lat, int prec, int op) {
   TileConfig t;
   t.spt = lat->Ls % 2 == 0 ? 2 : 1;
   t.tx = 32;
@@ -208,14 +213,18 @@ TileConfig cb_tile(const dw_lattice *lat, int prec, int op) {
   t.zblk = auto_zblk(lat, prec);
   const int nchunk = lat->Ls / t.spt;
   t.sgrp = 1;
-  if (op == OP_D)
+  if (op == OP_D && prec != DW_F64)
     for (int g : {3, 2})
-      if (nchunk % g == 0 && nchunk / g >= 1) {
+      if (nchunk % g == 0) {
         t.sgrp = g;
         break;
       }
-  if (prec == DW_F64) t.sgrp = 1;
   return t;
+}
+
+TileConfig cb_tile(const dw_lattice *lat, int prec, int op) {
+  auto it = lat->tuned.find(std::make_tuple(prec, kCbOpKey + op, 0));
+  return it != lat->tuned.end() ? it->second : cb_default_tile(lat, prec, op);
 }
 
 }  // namespace
@@ -284,9 +293,9 @@ long long cb_ctas_per_rhs(const dw_lattice *lat, int prec, int op) {
 int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr, const void *own,
                   int parity, double alpha, double beta, double hscale, const double *mf,
                   int nrhs, cudaStream_t st, const int *gate, int gate_stride,
-                  double *norm_partials) {
+                  double *norm_partials, const TileConfig *force) {
   const size_t rhs_bytes = cb_field_bytes(lat, prec, 1);
-  const TileConfig cfg = cb_tile(lat, prec, op);
+  const TileConfig cfg = force ? *force : cb_tile(lat, prec, op);
   const long long ctas = cb_ctas_per_rhs(lat, prec, op);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
     const int n = (nrhs - r0) < kMaxRhsPerLaunch ? (nrhs - r0) : kMaxRhsPerLaunch;
@@ -340,6 +349,65 @@ int apply_schur(dw_lattice *lat, int prec, void *out, const void *in, const doub
   // out = A in - H_oe t2  (A^+ in - H_eo^+ t2), on odd sites
   return run_dslash_cb(lat, prec, op, out, t2, in, 1, alpha, beta, 0.5, mf, nrhs, st, gate,
                        gate_stride, dag ? nullptr : norm_partials);
+}
+
+// Times the checkerboard tiles of (prec, op) on two scratch parity fields (the
+// hopping-only form, one RHS) and keeps the fastest for later launches.
+int tune_cb(dw_lattice *lat, int prec, int op, cudaStream_t st) {
+  if (lat->tuned.count(std::make_tuple(prec, kCbOpKey + op, 0))) return DW_OK;
+  const size_t bytes = cb_field_bytes(lat, prec, 1);
+  size_t cap_in = lat->stage_bytes, cap_out = lat->stage_bytes;
+  int rc = ensure_buffer(&lat->stage_in, &cap_in, bytes);
+  if (rc) return rc;
+  rc = ensure_buffer(&lat->stage_out, &cap_out, bytes);
+  if (rc) return rc;
+  lat->stage_bytes = cap_in < cap_out ? cap_in : cap_out;
+  if (cudaMemsetAsync(lat->stage_in, 0, bytes, st) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "tune memset");
+  const double mf = 0.01;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "event");
+  }
+  TileConfig best_t = cb_default_tile(lat, prec, op);
+  float best = 1e30f;
+  const int za = auto_zblk(lat, prec);
+  for (int spt : {1, 2, 3, 4})
+    for (int tx : {32, 64, 128})
+      for (int sgrp : {1, 2, 3, 4, 6}) {
+        if (lat->Ls % spt || (lat->Ls / spt) % sgrp || (op == OP_DDAG && sgrp != 1)) continue;
+        const TileConfig t{spt, tx, prec == DW_F64 ? 0 : 4, za, sgrp};
+        if (tx * (lat->Ls / spt / sgrp) > 1024) continue;
+        if (run_dslash_cb(lat, prec, op, lat->stage_out, lat->stage_in, nullptr, 0, 0.0, 0.0,
+                          -0.5, &mf, 1, st, nullptr, 0, nullptr, &t)) {
+          cudaGetLastError();
+          continue;  // not launchable (CTA limits)
+        }
+        float ms[3];
+        for (float &m : ms) {
+          cudaEventRecord(e0, st);
+          run_dslash_cb(lat, prec, op, lat->stage_out, lat->stage_in, nullptr, 0, 0.0, 0.0, -0.5,
+                        &mf, 1, st, nullptr, 0, nullptr, &t);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          m = 1e30f;
+          if (cudaEventElapsedTime(&m, e0, e1) != cudaSuccess) m = 1e30f;
+        }
+        std::sort(ms, ms + 3);
+        if (ms[1] < best) {
+          best = ms[1];
+          best_t = t;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  clear_error();
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "tune synchronize");
+  lat->tuned[std::make_tuple(prec, kCbOpKey + op, 0)] = best_t;
+  return DW_OK;
 }
 
 }  // namespace dw

@@ -165,6 +165,14 @@ int apply_host_pipelined(dw_lattice *lat, int op, void *out_host, const void *in
     }
     return cudaSuccess;
   };
+  // on an error after work was queued, let it drain before the host buffers
+  // go back to the caller
+  auto bail = [&](int code) {
+    cudaStreamSynchronize(lat->pipe_in);
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(lat->pipe_out);
+    return code;
+  };
   // the staging buffers may still be read by earlier work on the caller's stream
   cudaError_t e = cudaEventRecord(ev_start, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(lat->pipe_in, ev_start, 0);
@@ -173,23 +181,24 @@ int apply_host_pipelined(dw_lattice *lat, int op, void *out_host, const void *in
   for (int k = 0; k < n; ++k) {
     e = copy(lat->stage_in, in_host, k, cudaMemcpyHostToDevice, lat->pipe_in);
     if (e == cudaSuccess) e = cudaEventRecord(ev[k], lat->pipe_in);
-    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    if (e != cudaSuccess) return bail(cuda_fail(e, "host-to-device copy"));
   }
   for (size_t i = 0; i < tasks.size(); ++i) {
     const Task &t = tasks[i];
     if (t.wait_in >= 0) {
       e = cudaStreamWaitEvent(st, ev[t.wait_in], 0);
-      if (e != cudaSuccess) return cuda_fail(e, "pipeline ordering");
+      if (e != cudaSuccess) return bail(cuda_fail(e, "pipeline ordering"));
     }
-    rc = run_pass(lat, op, t.pass, lat->stage_out, lat->stage_in, mid, mf, nrhs, st, t.slab * T, T);
-    if (rc) return rc;
+    rc = run_pass(lat, op, t.pass, lat->stage_out, lat->stage_in, mid, mf, nrhs, st,
+                  t.slab * T, T);
+    if (rc) return bail(rc);
     e = cudaEventRecord(ev[n + i], st);
-    if (e != cudaSuccess) return cuda_fail(e, "pipeline ordering");
+    if (e != cudaSuccess) return bail(cuda_fail(e, "pipeline ordering"));
     if (t.pass == passes - 1) {  // the slab is final: copy it out
       e = cudaStreamWaitEvent(lat->pipe_out, ev[n + i], 0);
       if (e == cudaSuccess) e = copy(out_host, lat->stage_out, t.slab, cudaMemcpyDeviceToHost,
                                      lat->pipe_out);
-      if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+      if (e != cudaSuccess) return bail(cuda_fail(e, "device-to-host copy"));
     }
   }
   e = cudaStreamSynchronize(lat->pipe_out);

@@ -23,7 +23,7 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
   cudaEventCreate(&e1);
   float best = 1e30f;
   TileConfig best_t = default_tile(lat, prec, op, nrhs);
-  const int reps = 5;
+  const int reps = quick ? 3 : 5;
   // z-blockings: unblocked, the automatic one and twice that (quick: automatic)
   const int za = auto_zblk(lat, prec);
   std::vector<int> zbs{za};
