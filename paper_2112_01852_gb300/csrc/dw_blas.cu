@@ -106,16 +106,36 @@ __global__ void __launch_bounds__(kBlasThreads)
   if (threadIdx.x == 0) partial[(size_t)rhs * gridDim.x + blockIdx.x] = s;
 }
 
-// Fixed-order sum of the partials of one RHS by one warp.
+// Fixed-order sum of the partials of one RHS by one block of kSumThreads
+// threads (four independent strided accumulators per thread, then the warps,
+// then the warp sums in order); the result is valid in thread 0.  A stencil
+// launch can leave tens of thousands of partials per RHS.
+constexpr int kSumThreads = 256;
 __device__ __forceinline__ double sum_partials(const double *p, int n) {
-  double v = 0.0;
-  for (int k = threadIdx.x; k < n; k += 32) v += p[k];
+  __shared__ double ws[kSumThreads / 32];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = threadIdx.x;
+  for (; k + 3 * kSumThreads < n; k += 4 * kSumThreads) {
+    a0 += p[k];
+    a1 += p[k + kSumThreads];
+    a2 += p[k + 2 * kSumThreads];
+    a3 += p[k + 3 * kSumThreads];
+  }
+  for (; k < n; k += kSumThreads) a0 += p[k];
+  double v = (a0 + a1) + (a2 + a3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return __shfl_sync(0xffffffffu, v, 0);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < kSumThreads / 32 ? ws[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
 }
 
-// out[rhs] = sum of partials (one warp per RHS)
+// out[rhs] = sum of partials (one block per RHS)
 __global__ void finalize_sum_kernel(const double *partial, int nblk, double *out) {
   const int rhs = blockIdx.x;
   const double v = sum_partials(partial + (size_t)rhs * nblk, nblk);
@@ -438,7 +458,7 @@ int blas_redot(const BlasCtx &c, int pa, const void *a, int pb, const void *b, d
 }
 
 int blas_finalize_sum(const BlasCtx &c, const double *partial, double *out, cudaStream_t s) {
-  finalize_sum_kernel<<<c.nrhs, 32, 0, s>>>(partial, c.nblk, out);
+  finalize_sum_kernel<<<c.nrhs, kSumThreads, 0, s>>>(partial, c.nblk, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -488,19 +508,19 @@ int cg_direction(const BlasCtx &c, int pp, int pr, void *p, const void *r_s, con
 }
 
 int cg_alpha(const BlasCtx &c, const double *partial, int nblk, CGState *st, cudaStream_t s) {
-  cg_alpha_kernel<<<c.nrhs, 32, 0, s>>>(partial, nblk, st);
+  cg_alpha_kernel<<<c.nrhs, kSumThreads, 0, s>>>(partial, nblk, st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int cg_beta(const BlasCtx &c, const double *partial, CGState *st, double delta, double tol,
             int maxit, cudaStream_t s) {
-  cg_beta_kernel<<<c.nrhs, 32, 0, s>>>(partial, c.nblk, st, delta, tol, maxit);
+  cg_beta_kernel<<<c.nrhs, kSumThreads, 0, s>>>(partial, c.nblk, st, delta, tol, maxit);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int cg_reliable(const BlasCtx &c, const double *partial, CGState *st, double tol, int maxit,
                 int first, cudaStream_t s) {
-  cg_reliable_kernel<<<c.nrhs, 32, 0, s>>>(partial, c.nblk, st, tol, maxit, first,
+  cg_reliable_kernel<<<c.nrhs, kSumThreads, 0, s>>>(partial, c.nblk, st, tol, maxit, first,
                                            c.nreal);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
