@@ -303,9 +303,11 @@ def bench_cg(args, dims=None, Ls=None, seed=None):
                      x)
         x.zero_()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("cg_%s" % name)
         t0 = time.perf_counter()
         status, stats = lat.cg(x, bdev, [MF], nrhs=1, tol=1e-10, maxit=40000, mode=mode)
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
         xs = lat.unpack(x)
         Ax = oracle.dwdagdw(xs, U, dims, Ls, M5, B, C, [MF])
         res = float(np.linalg.norm((rhs - Ax).ravel()) / np.linalg.norm(rhs.ravel()))
@@ -347,9 +349,11 @@ def bench_eo(args):
                                                mode=mode), x)
         x.zero_()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("solve_%s" % name)
         t0 = time.perf_counter()
         status, stats = lat.solve_eo(x, e, [MF], nrhs=1, tol=1e-10, maxit=40000, mode=mode)
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
         out[name] = {"seconds": wall, "first_call_seconds": warm, "status": status,
                      "iters": stats[0].iters,
                      "reliable_updates": stats[0].reliable_updates,

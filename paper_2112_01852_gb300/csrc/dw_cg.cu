@@ -9,9 +9,10 @@
 // rescaled system A e = r / sigma with sigma = |r| / sqrt(n) (n reals per
 // RHS), so low-precision vectors hold entries of order one; x accumulates
 // x += sigma * e at each update.  A reliable update fires when the iterated
-// residual dropped below delta = 0.1 times its largest value since the last
-// update, when it claims convergence, or when maxit is reached; the FP64
-// residual b - D^+D x then decides convergence.
+// residual dropped below delta (0.01 with FP32 inner fields, 0.1 with FP16)
+// times its largest value since the last update, when it claims convergence,
+// or when maxit is reached; the FP64 residual b - D^+D x then decides
+// convergence.
 //
 // All per-RHS scalars live on the device (CGState); converged or stopped RHS
 // are masked off, and the stencil kernels skip their CTAs.  One inner
@@ -160,7 +161,11 @@ int cg_run(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs, 
            std::chrono::steady_clock::time_point t_start) {
   CGWork *w = lat->cg;
   cudaError_t e;
-  Solve S{lat, w, nrhs, mode, mode == DW_F64 ? DW_F64 : DW_F32, mode == DW_F64 ? 0.0 : 0.1,
+  // reliable-update threshold: 0.01 with FP32 inner fields, 0.1 with FP16
+  // ones (their rounding, 2^-11, would make the iterated residual drift too far
+  // over a longer stretch); both reach the same iteration counts
+  const double delta = mode == DW_F64 ? 0.0 : (mode == DW_F32 ? 0.01 : 0.1);
+  Solve S{lat, w, nrhs, mode, mode == DW_F64 ? DW_F64 : DW_F32, delta,
           tol, maxit, mf, w->stream,
           BlasCtx((int)(eo ? lat->V4 / 2 : lat->V4), lat->Ls, nrhs, lat->num_sms), eo};
   auto fbytes = [&](int prec, int n) {
