@@ -605,6 +605,19 @@ def main():
     del xw, yw
     latw.close()
 
+    # layout conversion (A0): canonical complex128 <-> internal FP32, device to device
+    canon = torch.zeros(V5 * 24, dtype=torch.float64, device="cuda")
+    canon_bytes = canon.numel() * 8
+    ms_pack = time_op(lambda: dw.dw_pack_fermion(lat.handle, y.data_ptr(), dw.DW_F32,
+                                                  canon.data_ptr(), 1, sh), args.steps, 3, stream)
+    ms_unpack = time_op(lambda: dw.dw_unpack_fermion(lat.handle, canon.data_ptr(), x.data_ptr(),
+                                                      dw.DW_F32, 1, sh), args.steps, 3, stream)
+    field_bytes = lat.fermion_bytes(1)
+    ops_out["pack_f32"] = {"ms": ms_pack, "gbs": (canon_bytes + field_bytes) / ms_pack / 1e6}
+    ops_out["unpack_f32"] = {"ms": ms_unpack,
+                             "gbs": (canon_bytes + field_bytes) / ms_unpack / 1e6}
+    del canon
+
     # end to end through the host-buffer entry point (pinned host, H2D + D2H inside)
     nbytes = lat.fermion_bytes(1)
     hin = x.cpu().pin_memory()
