@@ -229,19 +229,18 @@ __global__ void __launch_bounds__(kBlasThreads)
   }
 }
 
-// CG step: x_s += alpha p;  r_s -= alpha Ap;  partial |r_s|^2  (active RHS only)
+// CG step: r_s -= alpha Ap;  partial |r_s|^2  (active RHS only).  The
+// x_s += alpha p of the same step is done by cg_direction_kernel.
 template <class PP, class PR>
 __global__ void __launch_bounds__(kBlasThreads)
-    cg_update_kernel(void *x_s, void *r_s, const void *p, const void *Ap, SlotGeom L,
-                     size_t bpp, size_t bpr, double *partial, const CGState *st) {
+    cg_update_kernel(void *r_s, const void *Ap, SlotGeom L, size_t bpp, size_t bpr,
+                     double *partial, const CGState *st) {
   const int rhs = blockIdx.y;
   const CGState &S = st[rhs];
   double s = 0.0;
   if (S.run) {
     const double alpha = S.alpha;
-    void *pxs = RHS_PTR(char *, x_s, rhs, bpr);
     void *prs = RHS_PTR(char *, r_s, rhs, bpr);
-    const void *pp = RHS_PTR(const char *, p, rhs, bpp);
     const void *pap = RHS_PTR(const char *, Ap, rhs, bpp);
     using A = typename Arith<PP, PR>::T;
     const A a = (A)alpha;
@@ -249,18 +248,14 @@ __global__ void __launch_bounds__(kBlasThreads)
       A site = 0;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
-        A xv[4], rv[4], pv[4], av[4];
-        ld4<PR>(xv, pxs, q, i);
+        A rv[4], av[4];
         ld4<PR>(rv, prs, q, i);
-        ld4<PP>(pv, pp, q, i);
         ld4<PP>(av, pap, q, i);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          xv[k] += a * pv[k];
           rv[k] -= a * av[k];
           site += rv[k] * rv[k];
         }
-        st4<PR>(pxs, q, i, xv);
         st4<PR>(prs, q, i, rv);
       }
       s += (double)site;
@@ -270,27 +265,39 @@ __global__ void __launch_bounds__(kBlasThreads)
   if (threadIdx.x == 0) partial[(size_t)rhs * gridDim.x + blockIdx.x] = s;
 }
 
-// p = r_s + beta p  (active RHS that continue without a reliable update)
+// x_s += alpha p for every RHS whose step computed alpha (including those that
+// now wait for a reliable update), then p = r_s + beta p for those that go on
+// iterating: one read of p serves both.
 template <class PP, class PR>
 __global__ void __launch_bounds__(kBlasThreads)
-    cg_direction_kernel(void *p, const void *r_s, SlotGeom L, size_t bpp, size_t bpr,
-                        const CGState *st) {
+    cg_direction_kernel(void *p, void *x_s, const void *r_s, SlotGeom L, size_t bpp,
+                        size_t bpr, const CGState *st) {
   const int rhs = blockIdx.y;
   const CGState &S = st[rhs];
-  if (!S.run) return;
+  if (!S.xpend) return;
+  const bool next = S.run != 0;
   using A = typename Arith<PP, PR>::T;
+  const A a = (A)S.alpha;
   const A b = (A)S.beta;
   void *pp = RHS_PTR(char *, p, rhs, bpp);
+  void *pxs = RHS_PTR(char *, x_s, rhs, bpr);
   const void *prs = RHS_PTR(const char *, r_s, rhs, bpr);
   SLOT_LOOP(i) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      A pv[4], rv[4];
+      A pv[4], xv[4];
       ld4<PP>(pv, pp, q, i);
-      ld4<PR>(rv, prs, q, i);
+      ld4<PR>(xv, pxs, q, i);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) pv[k] = rv[k] + b * pv[k];
-      st4<PP>(pp, q, i, pv);
+      for (int k = 0; k < 4; ++k) xv[k] += a * pv[k];
+      st4<PR>(pxs, q, i, xv);
+      if (next) {
+        A rv[4];
+        ld4<PR>(rv, prs, q, i);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pv[k] = rv[k] + b * pv[k];
+        st4<PP>(pp, q, i, pv);
+      }
     }
   }
 }
@@ -304,6 +311,7 @@ __global__ void cg_alpha_kernel(const double *partial, int nblk, CGState *st) {
   const double pAp = sum_partials(partial + (size_t)rhs * nblk, nblk);
   if (threadIdx.x != 0) return;
   CGState &S = st[rhs];
+  S.xpend = 0;
   if (!S.run) return;
   S.pAp = pAp;
   if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(S.rr)) {
@@ -314,6 +322,7 @@ __global__ void cg_alpha_kernel(const double *partial, int nblk, CGState *st) {
     return;
   }
   S.alpha = S.rr / pAp;
+  S.xpend = 1;
 }
 
 // After the update: rr_new = |r_s|^2.  Flags a reliable update when the
@@ -489,21 +498,21 @@ int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int cg_update(const BlasCtx &c, int pp, int pr, void *x_s, void *r_s, const void *p,
-              const void *Ap, double *partial, const CGState *st, cudaStream_t s) {
+int cg_update(const BlasCtx &c, int pp, int pr, void *r_s, const void *Ap, double *partial,
+              const CGState *st, cudaStream_t s) {
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pp, PP, DISPATCH_PREC(pr, PR,
       cg_update_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
-          x_s, r_s, p, Ap, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), partial, st)));
+          r_s, Ap, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), partial, st)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int cg_direction(const BlasCtx &c, int pp, int pr, void *p, const void *r_s, const CGState *st,
-                 cudaStream_t s) {
+int cg_direction(const BlasCtx &c, int pp, int pr, void *p, void *x_s, const void *r_s,
+                 const CGState *st, cudaStream_t s) {
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pp, PP, DISPATCH_PREC(pr, PR,
       cg_direction_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
-          p, r_s, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), st)));
+          p, x_s, r_s, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), st)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -18,7 +18,7 @@ struct CGState {
   int breakdown;
   int iters;
   int reliable;
-  int pad;
+  int xpend;        // this iteration's x_s += alpha p is still due (set by cg_alpha)
   double rr;        // |r_s|^2 of the normalised residual
   double pAp;
   double alpha;
@@ -57,10 +57,13 @@ int cg_accumulate_x(const BlasCtx &c, int pr, void *x, const void *x_s, const CG
                     cudaStream_t s);
 int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r_s, void *x_s,
                       void *p, const CGState *st, cudaStream_t s);
-int cg_update(const BlasCtx &c, int pp, int pr, void *x_s, void *r_s, const void *p,
-              const void *Ap, double *partial, const CGState *st, cudaStream_t s);
-int cg_direction(const BlasCtx &c, int pp, int pr, void *p, const void *r_s, const CGState *st,
-                 cudaStream_t s);
+// r_s -= alpha Ap with |r_s|^2 partials; the x_s update waits for cg_direction,
+// which reads p once for x_s += alpha p and p = r_s + beta p (8 field passes
+// per iteration instead of 9).
+int cg_update(const BlasCtx &c, int pp, int pr, void *r_s, const void *Ap, double *partial,
+              const CGState *st, cudaStream_t s);
+int cg_direction(const BlasCtx &c, int pp, int pr, void *p, void *x_s, const void *r_s,
+                 const CGState *st, cudaStream_t s);
 // alpha = rr / <p, Ap> with <p, Ap> summed from nblk partials per RHS.
 int cg_alpha(const BlasCtx &c, const double *partial, int nblk, CGState *st, cudaStream_t s);
 int cg_beta(const BlasCtx &c, const double *partial, CGState *st, double delta, double tol,

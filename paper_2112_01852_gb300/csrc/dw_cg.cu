@@ -109,9 +109,9 @@ struct Solve {
     }
     if (rc) return rc;
     if (cg_alpha(c, w->dnorm, nd, w->state, st) ||
-        cg_update(c, pp, pr, w->xs, w->rs, w->p, w->Ap, w->partials, w->state, st) ||
+        cg_update(c, pp, pr, w->rs, w->Ap, w->partials, w->state, st) ||
         cg_beta(c, w->partials, w->state, delta, tol, maxit, st) ||
-        cg_direction(c, pp, pr, w->p, w->rs, w->state, st))
+        cg_direction(c, pp, pr, w->p, w->xs, w->rs, w->state, st))
       return cuda_fail(cudaGetLastError(), "cg iteration launch");
     return DW_OK;
   }
