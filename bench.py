@@ -322,28 +322,32 @@ def bench_cg(args, dims=None, Ls=None, seed=None):
     return out
 
 
-def bench_eo(args):
-    """D x = eta at 24^4 x Ls=16, m_f = 0.01, to 1e-10: even-odd preconditioned CG
-    (FP64 and mixed FP32 / FP16) against plain mixed-FP32 CG on D^+D x = D^+ eta;
-    every solution's residual |eta - D x| / |eta| is recomputed by the oracle."""
+def bench_eo(args, dims=None, Ls=None, seed=None, f64=True):
+    """D x = eta (default 24^4 x Ls=16, m_f = 0.01) to 1e-10: even-odd
+    preconditioned CG (FP64 unless f64 is False, mixed FP32 / FP16) against plain
+    mixed-FP32 CG on D^+D x = D^+ eta; every solution's residual |eta - D x| / |eta|
+    is recomputed by the oracle."""
     import oracle
     import torch
     from paper_2112_01852_gb300 import dw, inputs
     from paper_2112_01852_gb300.lattice import Lattice
-    U = inputs.exp_su3_field(CG_DIMS, seed=CG_SEED)
-    eta = inputs.gaussian_fermion(CG_DIMS, CG_LS, 1, seed=CG_SEED)
-    lat = Lattice(CG_DIMS, CG_LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
+    dims = CG_DIMS if dims is None else dims
+    Ls = CG_LS if Ls is None else Ls
+    seed = CG_SEED if seed is None else seed
+    U = inputs.exp_su3_field(dims, seed=seed)
+    eta = inputs.gaussian_fermion(dims, Ls, 1, seed=seed)
+    lat = Lattice(dims, Ls, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
     lat.load_gauge(U)
     e = lat.pack(eta)
-    out = {"workload": "mobius_solve_D_%s_ls%d_mf%g" % ("x".join(str(d) for d in CG_DIMS),
-                                                         CG_LS, MF), "tol": 1e-10}
+    out = {"workload": "mobius_solve_D_%s_ls%d_mf%g" % ("x".join(str(d) for d in dims),
+                                                         Ls, MF), "tol": 1e-10}
 
     def resid(x):
-        r = oracle.dw(lat.unpack(x), U, CG_DIMS, CG_LS, M5, B, C, [MF]) - eta
+        r = oracle.dw(lat.unpack(x), U, dims, Ls, M5, B, C, [MF]) - eta
         return float(np.linalg.norm(r.ravel()) / np.linalg.norm(eta.ravel()))
 
-    for name, mode in (("eo_f64", dw.DW_F64), ("eo_mixed_f32", dw.DW_F32),
-                       ("eo_mixed_f16", dw.DW_F16)):
+    modes = (("eo_f64", dw.DW_F64),) if f64 else ()
+    for name, mode in modes + (("eo_mixed_f32", dw.DW_F32), ("eo_mixed_f16", dw.DW_F16)):
         x = lat.empty(1)
         warm = _warm(lambda v, n: lat.solve_eo(v, e, [MF], nrhs=1, tol=1e-10, maxit=n,
                                                mode=mode), x)
@@ -648,6 +652,7 @@ def main():
         line["cg_eo"] = bench_eo(args)
         if args.cg_full:
             line["cg_full"] = bench_cg(args, DIMS, LS, SEED)
+            line["cg_eo_full"] = bench_eo(args, DIMS, LS, SEED, f64=False)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
