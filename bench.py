@@ -234,7 +234,7 @@ def run_reference(args):
     V4 = int(np.prod(DIMS))
     U = inputs.exp_su3_field(DIMS, seed=SEED)
     psi = inputs.gaussian_fermion(DIMS, LS, 1, seed=SEED)
-    nsite = 65536  # 4D sites per step (x Ls = 786432 site updates)
+    nsite = min(65536, V4)  # 4D sites per step (x Ls = 786432 site updates at full size)
     rng = np.random.default_rng(0)
     sites = np.sort(rng.choice(V4, size=nsite, replace=False))
     for _ in range(args.warmup):
@@ -252,8 +252,8 @@ def run_reference(args):
         "config": _config(),
         "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": "%d random 4D sites x Ls=12 per step of the 32^3x64 lattice"
-                                   % nsite},
+                         "sample": "%d random 4D sites x Ls=%d per step of the %s lattice"
+                                   % (nsite, LS, "x".join(str(d) for d in DIMS))},
         "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
