@@ -179,7 +179,9 @@ typedef struct {
  * updates, FP64 reductions and an FP64 true-residual convergence test.
  * Stops when |b - D^+D x| / |b| <= tol for every RHS (converged RHS are masked
  * off) or after maxit inner iterations.  stats[nrhs] (HOST) is filled.
- * Returns DW_OK, DW_ERR_NOT_CONVERGED or DW_ERR_BREAKDOWN.  Synchronises.
+ * Returns DW_OK, DW_ERR_NOT_CONVERGED, DW_ERR_BREAKDOWN, or DW_ERR_TIMEOUT when
+ * a stencil launch on this lattice gave up a bounded wait since the last
+ * dw_device_status (the word is then cleared).  Synchronises.
  */
 int dw_cg_solve(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs,
                 double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
@@ -222,14 +224,18 @@ int dw_apply_schur(dw_lattice *lat, void *out, const void *in, const double *mf,
 /*
  * Solve D x = eta with even-odd preconditioning: CG (mode as in dw_cg_solve:
  * FP64, or mixed FP32 / FP16 inner operator with FP64 reliable updates) on
- * Dhat^+ Dhat x_o = Dhat^+ (eta_o - H_oe A^-1 eta_e), stopped when the FP64
- * residual of that system is below tol relative to its right-hand side; then
- * x_e = A^-1 (eta_e - H_eo x_o).  x (start vector: its odd sites) and eta are
- * full DEVICE fields in the internal layout at DW_F64; mf[nrhs] HOST.  stats:
- * iters and reliable_updates of the odd-site CG, converged for that CG,
- * true_resid = |eta - D x| / |eta| recomputed in FP64 on the full lattice,
- * seconds for the whole call.  Needs even extents.  Returns DW_OK,
- * DW_ERR_NOT_CONVERGED or DW_ERR_BREAKDOWN.  Synchronises.
+ * Dhat^+ Dhat x_o = Dhat^+ (eta_o - H_oe A^-1 eta_e), then
+ * x_e = A^-1 (eta_e - H_eo x_o).  The solve targets the full system: after each
+ * CG pass the residual |eta - D x| / |eta| is recomputed in FP64 on the whole
+ * lattice, and while it is above tol (for any RHS) the CG runs again from the
+ * current x_o with its own tolerance lowered by the factor it missed by (at
+ * most 4 passes, maxit inner iterations in all).  x (start vector: its odd
+ * sites) and eta are full DEVICE fields in the internal layout at DW_F64;
+ * mf[nrhs] HOST.  stats: iters and reliable_updates of all CG passes,
+ * true_resid = |eta - D x| / |eta|, converged = (true_resid <= tol), seconds
+ * for the whole call.  Needs even extents.  Returns DW_OK, DW_ERR_NOT_CONVERGED
+ * (some RHS above tol), DW_ERR_BREAKDOWN or DW_ERR_TIMEOUT (as dw_cg_solve).
+ * Synchronises.
  */
 int dw_solve_eo(dw_lattice *lat, void *x, const void *eta, const double *mf, int nrhs,
                 double tol, int maxit, int mode, dw_cg_stats *stats, void *stream);
@@ -287,6 +293,20 @@ int dw_get_tile(dw_lattice *lat, int op, int prec, int nrhs, int *spt, int *tx, 
  * returns DW_OK or DW_ERR_TIMEOUT.
  */
 int dw_device_status(dw_lattice *lat);
+
+/*
+ * Bound of the first wait of each step of the row-staged stencil variants
+ * (6, 7, 8) on this lattice: polls >= 0 lets that wait give up after `polls`
+ * polls of the barrier, -1 (the default) restores the built-in bound of about a
+ * second.  A wait that gives up sets the lattice's status word (reported by
+ * dw_device_status, and by dw_cg_solve / dw_solve_eo as DW_ERR_TIMEOUT); the
+ * kernel then waits once more, with the built-in bound, for the copies it
+ * issued, so that it never reads or refills a slot with a copy in flight.
+ * polls = 0 therefore exercises the timeout report without losing the result:
+ * it exists for testing that path.  The paper has no counterpart.  Returns
+ * DW_OK or DW_ERR_ARG (polls < -1).
+ */
+int dw_set_wait_polls(dw_lattice *lat, int polls);
 
 /*
  * Domain decomposition along t on one device ("virtual ranks").  The hopping

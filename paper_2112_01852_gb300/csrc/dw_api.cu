@@ -142,6 +142,7 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     const int n = (nrhs - r0) < kMaxRhsPerLaunch ? (nrhs - r0) : kMaxRhsPerLaunch;
     DslashParams p;
     memset(&p, 0, sizeof(p));
+    p.wait_polls = -1;
     p.out = (char *)out + (size_t)r0 * rhs_bytes;
     p.in = (const char *)in + (size_t)r0 * rhs_bytes;
     p.gauge = lat->gauge[prec];
@@ -159,6 +160,7 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.t_begin = t_begin;
     p.t_count = t_count;
     p.status = lat->dev_status;
+    p.wait_polls = lat->wait_polls;
     p.own = p.in;
     p.alpha = lat->b * (4.0 - lat->M5) + 1.0;
     p.beta = lat->c * (4.0 - lat->M5) - 1.0;
@@ -263,6 +265,7 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
   lat->b = kind == DW_SHAMIR ? 1.0 : b;
   lat->c = kind == DW_SHAMIR ? 0.0 : c;
   lat->prec = prec;
+  lat->wait_polls = -1;
   cudaGetDevice(&lat->device);
   cudaDeviceGetAttribute(&lat->num_sms, cudaDevAttrMultiProcessorCount, lat->device);
   for (int p = 0; p < 3; ++p) {
@@ -414,6 +417,14 @@ int dw_device_status(dw_lattice *lat) {
   return DW_OK;
 }
 
+int dw_set_wait_polls(dw_lattice *lat, int polls) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (polls < -1) return fail(DW_ERR_ARG, "polls must be >= -1 (got %d)", polls);
+  lat->wait_polls = polls;
+  return DW_OK;
+}
+
 int dw_get_tile(dw_lattice *lat, int op, int prec, int nrhs, int *spt, int *tx, int *variant,
                 int *zblk, int *sgrp) {
   clear_error();
@@ -446,6 +457,7 @@ int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, 
   if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
   DslashParams p;
   memset(&p, 0, sizeof(p));
+  p.wait_polls = -1;
   p.in = in;
   p.gauge = lat->gauge[lat->prec];
   for (int m = 0; m < 4; ++m) p.bc[m] = lat->bc[m];

@@ -162,6 +162,7 @@ struct DslashParams {
   int t_begin;          // output sites: the time slices t_begin .. t_begin + t_count - 1
   int t_count;          // (0: all Lt; the inputs are read on the whole lattice)
   int *status;          // lattice-owned device word; set nonzero when a bounded wait gives up
+  int wait_polls;       // polls of the first bounded wait of a step (-1: the built-in bound)
   const void *own;      // field of the local term of D / D^+ (null: hopping term alone)
   int parity;           // checkerboard launches: parity of the output sites
   double alpha, beta;   // local term alpha psi + beta K psi (K^+ for D^+)
@@ -232,6 +233,7 @@ struct dw_lattice {
   int num_sms;
   bool gauge_loaded;
   int *dev_status;  // device word the kernels set when a bounded wait gives up
+  int wait_polls;   // dw_set_wait_polls (-1: the kernels' built-in bound)
   // gauge copies per precision (blocked; 18 reals per link at FP64, 12 below)
   void *gauge[3];
   // scratch: one field for D^+D, host-apply staging, reduction partials

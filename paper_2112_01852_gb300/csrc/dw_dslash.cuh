@@ -491,11 +491,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
 }
-// Wait for phase `parity` of the barrier; false after about a second or 2^24
-// polls, whichever comes first.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// Wait for phase `parity` of the barrier; false after about a second or
+// max_polls polls (default 2^24), whichever comes first.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          int max_polls = 1 << 24) {
   const long long t0 = clock64();
-  for (int i = 0; i < (1 << 24); ++i) {
+  for (int i = 0; i < max_polls; ++i) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -1091,7 +1092,10 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       hop_dir<P, 2, SB, true, false, false, SPT>(acc, F, gauge, (C)H.sign<2, false>(p),
                                                  H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls,
                                                  zero, zero, zero);
-      if (!mbar_wait(bar, (unsigned)k & 1u)) {
+      // p.wait_polls >= 0 bounds the first wait by that many polls (0: give up
+      // at once, which exercises the timeout report); the second bounded wait
+      // still lets the copies in flight land before the slots are read
+      if (!mbar_wait(bar, (unsigned)k & 1u, p.wait_polls >= 0 ? p.wait_polls : 1 << 24)) {
         atomicExch(p.status, 1);
         mbar_wait(bar, (unsigned)k & 1u);  // one more bounded wait for the copies in flight
       }

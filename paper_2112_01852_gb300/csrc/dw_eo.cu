@@ -301,6 +301,7 @@ int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr,
     const int n = (nrhs - r0) < kMaxRhsPerLaunch ? (nrhs - r0) : kMaxRhsPerLaunch;
     DslashParams p;
     memset(&p, 0, sizeof(p));
+    p.wait_polls = -1;
     p.out = (char *)out + (size_t)r0 * rhs_bytes;
     p.in = (const char *)nbr + (size_t)r0 * rhs_bytes;
     p.own = own ? (const char *)own + (size_t)r0 * rhs_bytes : nullptr;

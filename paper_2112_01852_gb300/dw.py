@@ -55,7 +55,7 @@ SYMBOLS = (
     "dw_cg_solve", "dw_set_tile", "dw_tune", "dw_device_status", "dw_halo_bytes",
     "dw_halo_pack", "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
     "dw_unpack_fermion", "dw_last_error", "dw_fermion_bytes_eo", "dw_eo_split", "dw_eo_merge",
-    "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo", "dw_get_tile",
+    "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo", "dw_get_tile", "dw_set_wait_polls",
 )
 
 
@@ -109,6 +109,7 @@ def load_library():
             "dw_tune": (I, [P, I, I, IP, IP, IP, IP, IP, P]),
             "dw_get_tile": (I, [P, I, I, I, IP, IP, IP, IP, IP]),
             "dw_device_status": (I, [P]),
+            "dw_set_wait_polls": (I, [P, I]),
             "dw_fermion_bytes_eo": (S, [P, I, I]),
             "dw_eo_split": (I, [P, P, P, P, I, I, P]),
             "dw_eo_merge": (I, [P, P, P, P, I, I, P]),
@@ -235,6 +236,10 @@ def dw_tune(lat, op, nrhs, stream=0):
 def dw_device_status(lat):
     """Raises DWError (DW_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
     _check(load_library().dw_device_status(lat))
+
+
+def dw_set_wait_polls(lat, polls):
+    _check(load_library().dw_set_wait_polls(lat, int(polls)))
 
 
 def dw_fermion_bytes_eo(lat, prec, nrhs):

@@ -179,6 +179,39 @@ def test_row_staged_variant_needs_lx32():
     lat.close()
 
 
+@pytest.mark.parametrize("op", [dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG], ids=["Dhop", "Dhop_dag"])
+def test_bounded_wait_timeout_is_reported(op):
+    # With the first bounded wait of each step limited to zero polls, every
+    # row-staged launch gives up that wait: the kernel records the timeout in
+    # the lattice's status word (DW_ERR_TIMEOUT from dw_device_status, once),
+    # then its second bounded wait lets the copies in flight land, so the
+    # result is still right.  With the built-in bound restored the status stays
+    # clear.
+    dims, Ls = (32, 4, 2, 4), 4
+    U, psi = make_case(dims, Ls, 1, seed=19)
+    ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.0])
+    lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
+    lat.load_gauge(U)
+    with pytest.raises(dw.DWError) as e:
+        dw.dw_set_wait_polls(lat.handle, -2)
+    assert e.value.code == dw.DW_ERR_ARG
+    for var in (6, 7):
+        lat.set_tile(op, 1, 32, var)
+        dw.dw_device_status(lat.handle)
+        dw.dw_set_wait_polls(lat.handle, 0)
+        got = run_gpu(lat, op, psi)
+        with pytest.raises(dw.DWError) as e:
+            dw.dw_device_status(lat.handle)
+        assert e.value.code == dw.DW_ERR_TIMEOUT, var
+        dw.dw_device_status(lat.handle)  # read and cleared: no second report
+        assert max_rel(got, ref) <= TOL[dw.DW_F32], var
+        dw.dw_set_wait_polls(lat.handle, -1)
+        got = run_gpu(lat, op, psi)
+        dw.dw_device_status(lat.handle)
+        assert max_rel(got, ref) <= TOL[dw.DW_F32], var
+    lat.close()
+
+
 def test_two_site_lattice_sums_coinciding_neighbours():
     # On a 2^4 lattice x+mu and x-mu are the same site: both hops must add.
     dims, Ls = (2, 2, 2, 2), 4
