@@ -204,6 +204,43 @@ def time_op(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def time_op_flushed(fn, steps, warmup, stream, flush):
+    """Mean ms per call over `steps` calls, each timed alone with CUDA events on
+    `stream` after `flush` (a device buffer larger than L2) has been rewritten, so
+    that no input of the call is L2-resident when it starts."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def paper_context():
+    """The paper's Domain Wall kernel rates on one A64FX node (Table 2, Sec. 4.2),
+    from the committed fixture: context for the GPU figures, not a target."""
+    path = os.path.join(ROOT, "tests", "golden", "table2_dwf_gflops.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t) for t in line.split()]
+            rows.append({"dims": v[:4], "Ls": v[4], "dp_1rank": v[5], "sp_1rank": v[6],
+                         "dp_4ranks": v[7], "sp_4ranks": v[8]})
+    return {"hardware": "one A64FX node (QPACE 4), 48 cores, HBM2 1 TB/s",
+            "unit": "GFlop/s", "source": "Table 2", "domain_wall_kernel": rows}
+
+
 def cpu_baseline(psi, U, budget_s=12.0):
     """The FP64 oracle's Dhop on the host cores: whole-lattice applies until the
     time budget is spent (at least one)."""
@@ -363,18 +400,27 @@ def bench_eo(args, dims=None, Ls=None, seed=None, f64=True):
                      "reliable_updates": stats[0].reliable_updates,
                      "true_resid": stats[0].true_resid, "oracle_resid": resid(x)}
         del x
-    # the same system without preconditioning: CG on D^+D x = D^+ eta
+    # the same system without preconditioning: CG on D^+D x = D^+ eta.  Its stopping
+    # test is on the normal equations, so its tolerance is lowered (and the solve
+    # rerun from zero) until the residual of D x = eta itself is at most 1e-10, the
+    # target the even-odd solve meets; the last, successful solve is the one timed.
     b = lat.empty(1)
     dw.dw_apply_Ddag(lat.handle, b.data_ptr(), e.data_ptr(), [MF], 1)
     y = lat.empty(1)
     _warm(lambda v, n: lat.cg(v, b, [MF], nrhs=1, tol=1e-10, maxit=n, mode=dw.DW_F32), y)
-    y.zero_()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    status, stats = lat.cg(y, b, [MF], nrhs=1, tol=1e-10, maxit=40000, mode=dw.DW_F32)
-    wall = time.perf_counter() - t0
+    tol_u = 1e-10
+    for _ in range(5):
+        y.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status, stats = lat.cg(y, b, [MF], nrhs=1, tol=tol_u, maxit=40000, mode=dw.DW_F32)
+        wall = time.perf_counter() - t0
+        r_full = resid(y)
+        if r_full <= 1e-10:
+            break
+        tol_u *= max(1e-3, min(0.5, 0.5 * 1e-10 / r_full))
     out["unprec_mixed_f32"] = {"seconds": wall, "status": status, "iters": stats[0].iters,
-                               "oracle_resid": resid(y)}
+                               "cg_tol": tol_u, "oracle_resid": r_full}
     out["speedup_eo_vs_unprec_mixed_f32"] = wall / out["eo_mixed_f32"]["seconds"]
     lat.close()
     return out
@@ -431,6 +477,27 @@ def bench_batched(args):
                            "iters": [s.iters for s in stats],
                            "reliable_updates": [s.reliable_updates for s in stats],
                            "max_oracle_resid": max(res)}
+    # the same 12 systems solved one after another (one RHS per solve)
+    seq, seq_res, seq_iters = 0.0, [], []
+    one = lat.empty(1)
+    _warm(lambda v, n: lat.cg(v, lat.pack(rhs[0]), [BATCH_MASSES[0]], nrhs=1, tol=1e-10,
+                              maxit=n, mode=dw.DW_F32), one)
+    for r in range(nrhs):
+        br = lat.pack(rhs[r])
+        one.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st1 = lat.cg(one, br, [BATCH_MASSES[r]], nrhs=1, tol=1e-10, maxit=40000,
+                        mode=dw.DW_F32)
+        seq += time.perf_counter() - t0
+        seq_iters.append(st1[0].iters)
+        sol1 = lat.unpack(one)
+        A1 = oracle.dwdagdw(sol1, U, BATCH_DIMS, BATCH_LS, M5, B, C, [BATCH_MASSES[r]])
+        seq_res.append(float(np.linalg.norm((rhs[r] - A1[0]).ravel())
+                             / np.linalg.norm(rhs[r].ravel())))
+    out["cg_sequential_mixed_f32"] = {"seconds": seq, "iters": seq_iters,
+                                      "max_oracle_resid": max(seq_res)}
+    out["batched_over_sequential_time"] = wall / seq
     lat.close()
     return out
 
@@ -569,13 +636,16 @@ def main():
     ops["DdagD"] = time_op(
         lambda: dw.dw_apply_DdagD(lat.handle, y.data_ptr(), x.data_ptr(), mf, 1, sh),
         max(5, args.steps // 2), 3, stream)
+    def op_line(ms, flop, nbytes):
+        gbs = nbytes / ms / 1e6
+        return {"ms": ms, "gflops": flop / ms / 1e6, "gbs": gbs, "frac": gbs / peak,
+                "bytes_per_launch": nbytes}
+
     ops_out = {
-        "D": {"ms": ops["D"], "gflops": FLOP_D_MOBIUS * V5 / ops["D"] / 1e6,
-              "gbs": alg_bytes / ops["D"] / 1e6},
-        "Ddag": {"ms": ops["Ddag"], "gflops": FLOP_D_MOBIUS * V5 / ops["Ddag"] / 1e6,
-                 "gbs": alg_bytes / ops["Ddag"] / 1e6},
-        "DdagD": {"ms": ops["DdagD"], "gflops": 2 * FLOP_D_MOBIUS * V5 / ops["DdagD"] / 1e6,
-                  "gbs": 2 * alg_bytes / ops["DdagD"] / 1e6},
+        "peak_gbs": peak, "peak_source": peak_kind + " copy bandwidth (MEASURED_PEAKS hbm_gbs)",
+        "D": op_line(ops["D"], FLOP_D_MOBIUS * V5, alg_bytes),
+        "Ddag": op_line(ops["Ddag"], FLOP_D_MOBIUS * V5, alg_bytes),
+        "DdagD": op_line(ops["DdagD"], 2 * FLOP_D_MOBIUS * V5, 2 * alg_bytes),
         "tiles": {"Dhop": tiles[dw.DW_OP_DHOP], "D": tiles.get(dw.DW_OP_D),
                   "Ddag": tiles.get(dw.DW_OP_DDAG)},
     }
@@ -593,20 +663,27 @@ def main():
     del x16, y16
     lat16.close()
 
-    # Wilson Dslash: the same kernel at Ls = 1 on the same 4D lattice
+    # Wilson Dslash: the same kernel at Ls = 1 on the same 4D lattice.  Its field
+    # (201 MB) and links (100 MB) would largely stay in L2 between back-to-back
+    # launches, so each launch is timed alone after an L2 flush.  The fraction is
+    # taken on the bytes the kernel must move: spinor in and out and two-row
+    # (12-real) links, 384 B per site (the 18-real model gives 480 B).
     latw = Lattice(DIMS, 1, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32)
     latw.load_gauge(U)
     psiw = inputs.gaussian_fermion(DIMS, 1, 1, seed=SEED)
     xw = latw.pack(psiw)
     yw = latw.empty(1)
     tw = latw.tune(dw.DW_OP_DHOP, 1)
-    msw = time_op(lambda: dw.dw_apply_Dhop(latw.handle, yw.data_ptr(), xw.data_ptr(), 1, sh),
-                  args.steps, 3, stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    msw = time_op_flushed(lambda: dw.dw_apply_Dhop(latw.handle, yw.data_ptr(), xw.data_ptr(),
+                                                   1, sh), max(10, args.steps // 2), 3, stream,
+                          flush)
+    moved = 4 * (48 + 48) * V4
     ops_out["wilson_dslash_f32"] = {"ms": msw, "gflops": FLOP_DHOP * V4 / msw / 1e6,
-                                    "gbs": bytes_per_site(4, 1) * V4 / msw / 1e6,
-                                    "frac": bytes_per_site(4, 1) * V4 / msw / 1e6 / peak,
+                                    "gbs": moved / msw / 1e6, "frac": moved / msw / 1e6 / peak,
+                                    "bytes_per_site": 384, "l2": "flushed before each launch",
                                     "tile": tw}
-    del xw, yw
+    del xw, yw, flush
     latw.close()
 
     # layout conversion (A0): canonical complex128 <-> internal FP32, device to device
@@ -617,9 +694,9 @@ def main():
     ms_unpack = time_op(lambda: dw.dw_unpack_fermion(lat.handle, canon.data_ptr(), x.data_ptr(),
                                                       dw.DW_F32, 1, sh), args.steps, 3, stream)
     field_bytes = lat.fermion_bytes(1)
-    ops_out["pack_f32"] = {"ms": ms_pack, "gbs": (canon_bytes + field_bytes) / ms_pack / 1e6}
-    ops_out["unpack_f32"] = {"ms": ms_unpack,
-                             "gbs": (canon_bytes + field_bytes) / ms_unpack / 1e6}
+    for name, msv in (("pack_f32", ms_pack), ("unpack_f32", ms_unpack)):
+        gbs = (canon_bytes + field_bytes) / msv / 1e6
+        ops_out[name] = {"ms": msv, "gbs": gbs, "frac": gbs / peak}
     del canon
 
     # end to end through the host-buffer entry point (pinned host, H2D + D2H inside)
@@ -642,6 +719,7 @@ def main():
 
     line["e2e"] = e2e
     line["ops"] = ops_out
+    line["paper_context"] = paper_context()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(psi, U)
     del x, y

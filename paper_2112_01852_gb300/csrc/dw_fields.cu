@@ -6,73 +6,115 @@ namespace dw {
 
 // ---------------------------------------------------------------------------
 // Canonical fermion complex128 [rhs][x4][s][spin][col] <-> internal planes.
-// One thread per (x4, s) of one RHS.  Internal real I = half*12 + c*4 + ri*2 + j
-// (chirality half, colour c, re/im ri, spin j within the half) holds the
-// canonical real ((2*half + j)*3 + c)*2 + ri: each 4-real quad is the spin
-// pair (Re j0, Re j1, Im j0, Im j1) of one colour.
-__device__ __forceinline__ int canon_real(int I) {
-  const int half = I / 12, i = I % 12;
-  const int c = i / 4, ri = (i % 4) / 2, j = i % 2;
-  return ((2 * half + j) * 3 + c) * 2 + ri;
+// Internal real I = half*12 + c*4 + ri*2 + j (chirality half, colour c, re/im
+// ri, spin j within the half) holds the canonical real
+// ((2*half + j)*3 + c)*2 + ri: each 4-real quad is the spin pair
+// (Re j0, Re j1, Im j0, Im j1) of one colour.
+//
+// Both directions are transposes of one 32-site block and kSC consecutive
+// slices per CTA through shared memory: the internal side of the chunk is one
+// contiguous run of vecs (coalesced 16-byte accesses, 8-byte at FP16), the
+// canonical side is kSC x 12 consecutive complex128 per site (coalesced
+// 16-byte accesses); the transpose itself happens in shared memory, one FP64
+// real per (site, slice, internal real I), rows padded to an odd length.
+constexpr int kSC = 4;        // slices per CTA
+constexpr int kXposeTPB = 128;
+constexpr int kLaneStride = kSC * 24 + 1;  // doubles per site row of the staging array
+
+// internal real of the real part of canonical complex kk (spin*3 + colour);
+// the imaginary part is the internal real two further on
+__device__ __forceinline__ int internal_re(int kk) {
+  const int spin = kk / 3, c = kk % 3;
+  return (spin >> 1) * 12 + c * 4 + (spin & 1);
 }
+
 template <class P>
-__global__ void pack_kernel(typename P::vec *dst, const double *src, long long V5, int V4,
-                            int Ls, long long rhs_stride) {
+__global__ void __launch_bounds__(kXposeTPB) pack_kernel(typename P::vec *dst,
+                                                         const double2 *src, int V4, int Ls,
+                                                         long long rhs_stride, long long V5) {
   constexpr int NP = 24 / P::R;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  __shared__ double sm[32 * kLaneStride];
+  const int nch = (Ls + kSC - 1) / kSC;
+  const int blk = (int)(blockIdx.x / nch);
+  const int s0 = (int)(blockIdx.x % nch) * kSC;
+  const int sc = min(kSC, Ls - s0);
   const int rhs = blockIdx.y;
-  if (i >= V5) return;
-  const int x4 = (int)(i / Ls);
-  const int s = (int)(i % Ls);
-  const double *p = src + ((long long)rhs * V5 + i) * 24;
-  typename P::vec *d = dst + (long long)rhs * rhs_stride + site_off(x4, s, Ls, NP);
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
+  // canonical -> staging: consecutive threads read consecutive complex128
+  const int nin = 32 * sc * 12;
+  for (int o = threadIdx.x; o < nin; o += kXposeTPB) {
+    const int lane = o / (sc * 12), rem = o % (sc * 12), sl = rem / 12, kk = rem % 12;
+    const int x4 = blk * 32 + lane;
+    if (x4 >= V4) continue;
+    const double2 v = __ldcs(src + ((long long)rhs * V5 + (long long)x4 * Ls + s0 + sl) * 12 + kk);
+    double *b = sm + lane * kLaneStride + sl * 24 + internal_re(kk);
+    b[0] = v.x;
+    b[2] = v.y;
+  }
+  __syncthreads();
+  // staging -> internal: the chunk is one contiguous run of sc * NP * 32 vecs
+  typename P::vec *dp = dst + rhs * rhs_stride + ((long long)blk * Ls + s0) * NP * 32;
+  for (int v = threadIdx.x; v < sc * NP * 32; v += kXposeTPB) {
+    const int lane = v & 31, q = (v >> 5) % NP, sl = (v >> 5) / NP;
+    if (blk * 32 + lane >= V4) continue;  // padding lanes are never written
     double r[P::R];
 #pragma unroll
-    for (int k = 0; k < P::R; ++k) r[k] = p[canon_real(q * P::R + k)];
-    d[q * kPlaneStride] = narrow_from_f64(r, (typename P::vec *)nullptr);
+    for (int w = 0; w < P::R; ++w) r[w] = sm[lane * kLaneStride + sl * 24 + q * P::R + w];
+    dp[v] = narrow_from_f64(r, (typename P::vec *)nullptr);
   }
 }
 
 template <class P>
-__global__ void unpack_kernel(double *dst, const typename P::vec *src, long long V5, int V4,
-                              int Ls, long long rhs_stride) {
+__global__ void __launch_bounds__(kXposeTPB) unpack_kernel(double2 *dst,
+                                                           const typename P::vec *src, int V4,
+                                                           int Ls, long long rhs_stride,
+                                                           long long V5) {
   using C = typename P::C;
   constexpr int NP = 24 / P::R;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  __shared__ double sm[32 * kLaneStride];
+  const int nch = (Ls + kSC - 1) / kSC;
+  const int blk = (int)(blockIdx.x / nch);
+  const int s0 = (int)(blockIdx.x % nch) * kSC;
+  const int sc = min(kSC, Ls - s0);
   const int rhs = blockIdx.y;
-  if (i >= V5) return;
-  const int x4 = (int)(i / Ls);
-  const int s = (int)(i % Ls);
-  double *p = dst + ((long long)rhs * V5 + i) * 24;
-  const typename P::vec *sp = src + (long long)rhs * rhs_stride + site_off(x4, s, Ls, NP);
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
+  // internal -> staging
+  const typename P::vec *sp = src + rhs * rhs_stride + ((long long)blk * Ls + s0) * NP * 32;
+  for (int v = threadIdx.x; v < sc * NP * 32; v += kXposeTPB) {
+    const int lane = v & 31, q = (v >> 5) % NP, sl = (v >> 5) / NP;
+    if (blk * 32 + lane >= V4) continue;
     C r[P::R];
-    load_vec<P>(r, sp + q * kPlaneStride);
+    load_vec<P>(r, sp + v);
 #pragma unroll
-    for (int k = 0; k < P::R; ++k) p[canon_real(q * P::R + k)] = (double)r[k];
+    for (int w = 0; w < P::R; ++w) sm[lane * kLaneStride + sl * 24 + q * P::R + w] = (double)r[w];
+  }
+  __syncthreads();
+  // staging -> canonical: consecutive threads write consecutive complex128
+  const int nout = 32 * sc * 12;
+  for (int o = threadIdx.x; o < nout; o += kXposeTPB) {
+    const int lane = o / (sc * 12), rem = o % (sc * 12), sl = rem / 12, kk = rem % 12;
+    const int x4 = blk * 32 + lane;
+    if (x4 >= V4) continue;
+    const double *b = sm + lane * kLaneStride + sl * 24 + internal_re(kk);
+    __stcs(dst + ((long long)rhs * V5 + (long long)x4 * Ls + s0 + sl) * 12 + kk,
+           make_double2(b[0], b[2]));
   }
 }
 
 template <class P>
 static int pack_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cudaStream_t st) {
-  const long long V5 = g.V5();
-  const int tpb = 256;
-  dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
-  pack_kernel<P><<<grid, tpb, 0, st>>>((typename P::vec *)dst, (const double *)src, V5, g.V4,
-                                       g.Ls, padded_v4(g.V4) * g.Ls * (24 / P::R));
+  const long long nch = (g.Ls + kSC - 1) / kSC;
+  dim3 grid((unsigned)(padded_v4(g.V4) / 32 * nch), nrhs);
+  pack_kernel<P><<<grid, kXposeTPB, 0, st>>>((typename P::vec *)dst, (const double2 *)src, g.V4,
+                                             g.Ls, padded_v4(g.V4) * g.Ls * (24 / P::R), g.V5());
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <class P>
 static int unpack_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cudaStream_t st) {
-  const long long V5 = g.V5();
-  const int tpb = 256;
-  dim3 grid((unsigned)((V5 + tpb - 1) / tpb), nrhs);
-  unpack_kernel<P><<<grid, tpb, 0, st>>>((double *)dst, (const typename P::vec *)src, V5, g.V4,
-                                         g.Ls, padded_v4(g.V4) * g.Ls * (24 / P::R));
+  const long long nch = (g.Ls + kSC - 1) / kSC;
+  dim3 grid((unsigned)(padded_v4(g.V4) / 32 * nch), nrhs);
+  unpack_kernel<P><<<grid, kXposeTPB, 0, st>>>((double2 *)dst, (const typename P::vec *)src,
+                                               g.V4, g.Ls,
+                                               padded_v4(g.V4) * g.Ls * (24 / P::R), g.V5());
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
