@@ -524,6 +524,9 @@ def main():
                     help="time only the FP32 Dhop (no other operators, e2e, CG or CPU leg)")
     ap.add_argument("--tile", default=None,
                     help="spt,tx[,variant[,zblk[,sgrp]]]: fixed Dhop tile instead of tuning")
+    ap.add_argument("--layout", default="spin_pair", choices=["spin_pair", "complex"],
+                    help="FP32 quad layout of the timed Dhop (complex: the interleaved-"
+                         "complex layout of the ablation)")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--cg-full", action="store_true",
                     help="also run the three CGs on the benchmark lattice (minutes)")
@@ -559,6 +562,8 @@ def main():
     sh = stream.cuda_stream
     lat = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32)
     lat.load_gauge(U)
+    if args.layout == "complex":
+        dw.dw_set_complex_layout(lat.handle, 1)
     x = lat.pack(psi)
     y = lat.empty(1)
     tiles = {}
@@ -619,7 +624,8 @@ def main():
         "clocks": clocks,
         "tile": tiles[dw.DW_OP_DHOP],
     }
-    if args.main_only:
+    if args.main_only or args.layout != "spin_pair":
+        line["layout"] = args.layout
         if rank == 0:
             print(json.dumps(line), flush=True)
         lat.close()
@@ -649,6 +655,23 @@ def main():
         "tiles": {"Dhop": tiles[dw.DW_OP_DHOP], "D": tiles.get(dw.DW_OP_D),
                   "Ddag": tiles.get(dw.DW_OP_DDAG)},
     }
+    # layout ablation: the same Dhop with interleaved-complex quads (the RIRI
+    # counterpart) at its own tuned tile, beside the spin-pair (RRII-like) default
+    latc = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32)
+    latc.load_gauge(U)
+    dw.dw_set_complex_layout(latc.handle, 1)
+    xc = latc.pack(psi)
+    yc = latc.empty(1)
+    tc = latc.tune(dw.DW_OP_DHOP, 1)
+    msc = time_op(lambda: dw.dw_apply_Dhop(latc.handle, yc.data_ptr(), xc.data_ptr(), 1, sh),
+                  args.steps, 3, stream)
+    ops_out["layout_ablation"] = {
+        "spin_pair": dict(op_line(ms, FLOP_DHOP * V5, alg_bytes), tile=tiles[dw.DW_OP_DHOP]),
+        "interleaved_complex": dict(op_line(msc, FLOP_DHOP * V5, alg_bytes), tile=tc),
+    }
+    del xc, yc
+    latc.close()
+
     # FP16-storage Dhop on the same lattice
     lat16 = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F16)
     lat16.load_gauge(U)

@@ -295,6 +295,26 @@ int dw_get_tile(dw_lattice *lat, int op, int prec, int nrhs, int *spt, int *tx, 
 int dw_device_status(dw_lattice *lat);
 
 /*
+ * Layout ablation: the interleaved-complex form of the fermion quads (the GPU
+ * counterpart of the paper's RIRI layout, Sec. 4.3, Table 3).  By default a quad
+ * of the internal layout is the spin pair (Re j0, Re j1, Im j0, Im j1) of one
+ * colour and chirality half, and the stencil's packed FP32 arithmetic pairs
+ * the two spins (the counterpart of RRII: real arithmetic only).  With
+ * interleaved = 1 the FP32 fields of this DW_F32 lattice hold
+ * (Re j0, Im j0, Re j1, Im j1) instead, and the stencil pairs the real and
+ * imaginary parts of one complex number (a product by i swaps a pair; a complex
+ * product needs the pair and its swapped copy).  Only dw_pack_fermion /
+ * dw_unpack_fermion at DW_F32, dw_apply_Dhop, dw_apply_Dhop_dag, dw_apply_host
+ * with those operators, dw_set_tile / dw_tune (variants 4-7) and the size queries
+ * support it; the other operators, the even-odd calls and the solvers return
+ * DW_ERR_STATE.  Fields packed under one setting must not be used under the
+ * other.  Switching clears the lattice's tuned tiles.  interleaved = 0 restores
+ * the default.  Returns DW_OK or DW_ERR_ARG (not a DW_F32 lattice, or
+ * interleaved not 0 / 1).
+ */
+int dw_set_complex_layout(dw_lattice *lat, int interleaved);
+
+/*
  * Bound of the first wait of each step of the row-staged stencil variants
  * (6, 7, 8) on this lattice: polls >= 0 lets that wait give up after `polls`
  * polls of the barrier, -1 (the default) restores the built-in bound of about a

@@ -78,10 +78,13 @@ TileConfig default_tile(const dw_lattice *lat, int prec, int op, int nrhs) {
   (void)nrhs;
   const int Ls = lat->Ls;
   TileConfig t{0, 32, 0, auto_zblk(lat, prec), 1};
+  // interleaved-complex FP32 fields: the capped register variant
+  const bool cx = lat->cplx && prec == DW_F32;
+  if (cx) t.variant = 5;
   int maxt = 0;
   for (int spt : {1, 2, 3, 4}) {
     if (Ls % spt) continue;
-    const int m = dslash_max_threads(prec, op, spt, 0);
+    const int m = dslash_max_threads(prec, op, spt, t.variant);
     if ((Ls / spt) * 32 <= m) {
       t.spt = spt;
       maxt = m;
@@ -107,6 +110,7 @@ TileConfig pick_tile(dw_lattice *lat, int prec, int op, int nrhs) {
 
 bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (t.spt < 1 || t.spt > 4 || lat->Ls % t.spt) return false;
+  if (lat->cplx && prec == DW_F32 && !cplx_variant_ok(op, t.variant)) return false;
   if (t.tx < 32 || t.tx % 32) return false;
   if (t.variant < 0 || t.variant > kNumVariants - 1) return false;
   if (t.zblk < 1 || lat->dims[2] % t.zblk) return false;
@@ -172,7 +176,16 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     const TileConfig cfg = force ? *force : pick_tile(lat, prec, op, nrhs);
     p.norm_partials =
         norm_partials ? norm_partials + (size_t)r0 * dslash_ctas_per_rhs(lat, cfg) : nullptr;
-    const int rc = launch_dslash(p, prec, op, cfg, st);
+    int rc;
+    if (lat->cplx && prec == DW_F32) {
+      if (op != OP_DHOP && op != OP_DHOP_DAG)
+        return fail(DW_ERR_STATE,
+                    "interleaved-complex FP32 fields (dw_set_complex_layout) support Dhop and "
+                    "Dhop^+ only");
+      rc = launch_dslash_cplx(p, op, cfg, st);
+    } else {
+      rc = launch_dslash(p, prec, op, cfg, st);
+    }
     if (rc == -2)
       return fail(DW_ERR_ARG, "unsupported tile (spt=%d, tx=%d, variant=%d, zblk=%d) for Ls=%d",
                   cfg.spt, cfg.tx, cfg.variant, cfg.zblk, lat->Ls);
@@ -266,6 +279,7 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
   lat->c = kind == DW_SHAMIR ? 0.0 : c;
   lat->prec = prec;
   lat->wait_polls = -1;
+  lat->cplx = false;
   cudaGetDevice(&lat->device);
   cudaDeviceGetAttribute(&lat->num_sms, cudaDevAttrMultiProcessorCount, lat->device);
   for (int p = 0; p < 3; ++p) {
@@ -417,6 +431,17 @@ int dw_device_status(dw_lattice *lat) {
   return DW_OK;
 }
 
+int dw_set_complex_layout(dw_lattice *lat, int interleaved) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (interleaved != 0 && interleaved != 1) return fail(DW_ERR_ARG, "interleaved must be 0 or 1");
+  if (interleaved && lat->prec != DW_F32)
+    return fail(DW_ERR_ARG, "the interleaved-complex layout exists for DW_F32 lattices only");
+  lat->cplx = interleaved != 0;
+  lat->tuned.clear();  // tiles tuned for the other layout no longer apply
+  return DW_OK;
+}
+
 int dw_set_wait_polls(dw_lattice *lat, int polls) {
   clear_error();
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
@@ -455,6 +480,8 @@ int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, 
     return fail(DW_ERR_ARG, "buffers must be 16-byte aligned");
   if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
   if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  if (lat->cplx && lat->prec == DW_F32)
+    return fail(DW_ERR_STATE, "interleaved-complex FP32 fields support Dhop and Dhop^+ only");
   DslashParams p;
   memset(&p, 0, sizeof(p));
   p.wait_polls = -1;
@@ -505,7 +532,8 @@ int dw_pack_fermion(dw_lattice *lat, void *dst_internal, int prec, const void *s
   if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
   if (!aligned16(dst_internal) || !aligned16(src_c128))
     return fail(DW_ERR_ARG, "fields must be 16-byte aligned");
-  if (pack_fermion(geom(lat), prec, dst_internal, src_c128, nrhs, (cudaStream_t)stream))
+  if (pack_fermion(geom(lat), prec, dst_internal, src_c128, nrhs, (cudaStream_t)stream,
+                   lat->cplx && prec == DW_F32))
     return cuda_fail(cudaGetLastError(), "pack launch");
   return DW_OK;
 }
@@ -519,7 +547,8 @@ int dw_unpack_fermion(dw_lattice *lat, void *dst_c128, const void *src_internal,
   if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
   if (!aligned16(dst_c128) || !aligned16(src_internal))
     return fail(DW_ERR_ARG, "fields must be 16-byte aligned");
-  if (unpack_fermion(geom(lat), prec, dst_c128, src_internal, nrhs, (cudaStream_t)stream))
+  if (unpack_fermion(geom(lat), prec, dst_c128, src_internal, nrhs, (cudaStream_t)stream,
+                     lat->cplx && prec == DW_F32))
     return cuda_fail(cudaGetLastError(), "unpack launch");
   return DW_OK;
 }

@@ -349,6 +349,8 @@ int cg_prepare(dw_lattice *lat, void *x, const void *b, const double *mf, int nr
   if (mode != DW_F64 && mode != DW_F32 && mode != DW_F16)
     return fail(DW_ERR_ARG, "unknown mode %d", mode);
   if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  if (lat->cplx)
+    return fail(DW_ERR_STATE, "the solvers need the spin-pair layout (dw_set_complex_layout 0)");
   if (!lat->cg) lat->cg = new (std::nothrow) CGWork();
   CGWork *w = lat->cg;
   if (!w) return fail(DW_ERR_ALLOC, "host allocation failed");

@@ -28,6 +28,7 @@ struct F64 {
   static constexpr int RB = 8;  // bytes per real
   static constexpr int NLV = 9;
   static constexpr bool LINK12 = false;
+  static constexpr bool CPLX = false;
   static constexpr int id = DW_F64;
 };
 struct F32 {
@@ -37,7 +38,13 @@ struct F32 {
   static constexpr int RB = 4;
   static constexpr int NLV = 3;
   static constexpr bool LINK12 = true;
+  static constexpr bool CPLX = false;
   static constexpr int id = DW_F32;
+};
+// FP32 storage with interleaved-complex quads (Re j0, Im j0, Re j1, Im j1) and
+// complex-form arithmetic: the layout ablation (dw_set_complex_layout).
+struct F32C : F32 {
+  static constexpr bool CPLX = true;
 };
 struct F16 {
   using vec = uint2;  // 4 x binary16
@@ -46,6 +53,7 @@ struct F16 {
   static constexpr int RB = 2;
   static constexpr int NLV = 3;
   static constexpr bool LINK12 = true;
+  static constexpr bool CPLX = false;
   static constexpr int id = DW_F16;
 };
 inline int prec_link_vecs(int prec) { return prec == DW_F64 ? 9 : 3; }
@@ -201,6 +209,12 @@ inline size_t rows_smem_bytes(int tx, int nsl, int prec) {
 // that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA
 // launch error.
 int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
+// Stencil on interleaved-complex FP32 fields (layout ablation): Dhop / Dhop^+
+// with variants 4-7 only; same return codes.
+int launch_dslash_cplx(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+inline bool cplx_variant_ok(int op, int variant) {
+  return (op == OP_DHOP || op == OP_DHOP_DAG) && variant >= 4 && variant <= 7;
+}
 // Checkerboard (single-parity) stencil, OP_D / OP_DDAG forms only.
 int launch_dslash_cb(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
 // Largest CTA the stencil kernel (op, spt, variant) can launch (0: none).
@@ -234,6 +248,7 @@ struct dw_lattice {
   bool gauge_loaded;
   int *dev_status;  // device word the kernels set when a bounded wait gives up
   int wait_polls;   // dw_set_wait_polls (-1: the kernels' built-in bound)
+  bool cplx;        // dw_set_complex_layout: FP32 fields hold interleaved-complex quads
   // gauge copies per precision (blocked; 18 reals per link at FP64, 12 below)
   void *gauge[3];
   // scratch: one field for D^+D, host-apply staging, reduction partials

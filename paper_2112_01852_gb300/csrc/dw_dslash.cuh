@@ -59,15 +59,21 @@ __device__ __forceinline__ V2 pr(C x, C y) {
   return r;
 }
 
-template <class V2>
+// CX = false: the spin-pair form above.  CX = true: the interleaved-complex
+// form of the layout ablation, z[c][j] = (Re, Im) of spin j, colour c.
+template <class V2, bool CX = false>
 struct Half {
   V2 re[3];
   V2 im[3];
 };
 template <class V2>
+struct Half<V2, true> {
+  V2 z[3][2];
+};
+template <class V2, bool CX = false>
 struct Spinor {
-  Half<V2> up;  // spins 0, 1 (P+)
-  Half<V2> lo;  // spins 2, 3 (P-)
+  Half<V2, CX> up;  // spins 0, 1 (P+)
+  Half<V2, CX> lo;  // spins 2, 3 (P-)
 };
 
 template <class P>
@@ -75,6 +81,10 @@ struct Pair {
   using type = typename std::conditional<std::is_same<typename P::C, double>::value, double2,
                                          float2>::type;
 };
+template <class P>
+using HalfP = Half<typename Pair<P>::type, P::CPLX>;
+template <class P>
+using SpinorP = Spinor<typename Pair<P>::type, P::CPLX>;
 
 // h = u + S e_mu l   (the half spinor of (1 + S g_mu) psi)
 template <int MU, int S, class V2>
@@ -179,6 +189,104 @@ __device__ __forceinline__ void su3_mul(Half<V2> &w, const C *U, const Half<V2> 
     }
     w.re[r] = wr;
     w.im[r] = wi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Interleaved-complex form (layout ablation, the counterpart of the paper's
+// RIRI layout; the forms above are its RRII counterpart).  A register pair is
+// one complex number (Re, Im); multiplying by +-i swaps the pair's halves, and
+// a complex product takes two packed FMAs on the pair and on its swapped copy.
+template <class V2>
+__device__ __forceinline__ V2 swz(V2 a) {
+  return pr<V2>(a.y, a.x);
+}
+
+// h = u + S e_mu l   (see project above)
+template <int MU, int S, class V2>
+__device__ __forceinline__ void project(Half<V2, true> &h, const Half<V2, true> &u,
+                                        const Half<V2, true> &l) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) {  // e l = (i l1, i l0)
+      h.z[c][0] = p_fma(pr<V2>(-S, S), swz(l.z[c][1]), u.z[c][0]);
+      h.z[c][1] = p_fma(pr<V2>(-S, S), swz(l.z[c][0]), u.z[c][1]);
+    } else if (MU == 1) {  // e l = (l1, -l0)
+      h.z[c][0] = p_fma(bc<V2>(S), l.z[c][1], u.z[c][0]);
+      h.z[c][1] = p_fma(bc<V2>(-S), l.z[c][0], u.z[c][1]);
+    } else if (MU == 2) {  // e l = (i l0, -i l1)
+      h.z[c][0] = p_fma(pr<V2>(-S, S), swz(l.z[c][0]), u.z[c][0]);
+      h.z[c][1] = p_fma(pr<V2>(S, -S), swz(l.z[c][1]), u.z[c][1]);
+    } else {  // e l = l
+      h.z[c][0] = p_fma(bc<V2>(S), l.z[c][0], u.z[c][0]);
+      h.z[c][1] = p_fma(bc<V2>(S), l.z[c][1], u.z[c][1]);
+    }
+  }
+}
+
+// acc += (w, S e_mu^+ w)   (FIRST: acc = ...)
+template <int MU, int S, bool FIRST, class V2>
+__device__ __forceinline__ void reconstruct(Spinor<V2, true> &acc, const Half<V2, true> &w) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc.up.z[c][j] = FIRST ? w.z[c][j] : p_add(acc.up.z[c][j], w.z[c][j]);
+    // lower-spin increment S e^+ w: the factor and the source of each spin
+    V2 f0, f1, a0, a1;
+    if (MU == 0) {  // e^+ w = (-i w1, -i w0)
+      f0 = pr<V2>(S, -S); a0 = swz(w.z[c][1]);
+      f1 = pr<V2>(S, -S); a1 = swz(w.z[c][0]);
+    } else if (MU == 1) {  // e^+ w = (-w1, w0)
+      f0 = bc<V2>(-S); a0 = w.z[c][1];
+      f1 = bc<V2>(S); a1 = w.z[c][0];
+    } else if (MU == 2) {  // e^+ w = (-i w0, i w1)
+      f0 = pr<V2>(S, -S); a0 = swz(w.z[c][0]);
+      f1 = pr<V2>(-S, S); a1 = swz(w.z[c][1]);
+    } else {  // e^+ w = w
+      f0 = bc<V2>(S); a0 = w.z[c][0];
+      f1 = bc<V2>(S); a1 = w.z[c][1];
+    }
+    if (FIRST) {
+      acc.lo.z[c][0] = p_mul(f0, a0);
+      acc.lo.z[c][1] = p_mul(f1, a1);
+    } else {
+      acc.lo.z[c][0] = p_fma(f0, a0, acc.lo.z[c][0]);
+      acc.lo.z[c][1] = p_fma(f1, a1, acc.lo.z[c][1]);
+    }
+  }
+}
+
+// w = U h (ADJ = false) or U^+ h (ADJ = true), both spins; (ur + i ui) z is
+// ur (Re z, Im z) + (-ui, ui) (Im z, Re z).
+template <bool ADJ, class V2, class C>
+__device__ __forceinline__ void su3_mul(Half<V2, true> &w, const C *U, const Half<V2, true> &h) {
+  V2 hs[3][2];  // the swapped copies, shared by the three rows
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    hs[k][0] = swz(h.z[k][0]);
+    hs[k][1] = swz(h.z[k][1]);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    V2 w0, w1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int idx = ADJ ? (k * 3 + r) : (r * 3 + k);
+      const C ur = U[idx * 2];
+      const C ui = ADJ ? -U[idx * 2 + 1] : U[idx * 2 + 1];
+      const V2 vi = pr<V2>(-ui, ui);
+      if (k == 0) {
+        w0 = p_mul(bc<V2>(ur), h.z[k][0]);
+        w1 = p_mul(bc<V2>(ur), h.z[k][1]);
+      } else {
+        w0 = p_fma(bc<V2>(ur), h.z[k][0], w0);
+        w1 = p_fma(bc<V2>(ur), h.z[k][1], w1);
+      }
+      w0 = p_fma(vi, hs[k][0], w0);
+      w1 = p_fma(vi, hs[k][1], w1);
+    }
+    w.z[r][0] = w0;
+    w.z[r][1] = w1;
   }
 }
 
@@ -306,16 +414,35 @@ struct Field {
     for (int c = 0; c < 3; ++c)
       quad_in_h<HINT>(h.re[c], h.im[c], p + (long long)c * VPQ * plane, plane, pol);
   }
+  // interleaved-complex quads (Re j0, Im j0, Re j1, Im j1): FP32 storage only
+  template <int HINT>
+  __device__ __forceinline__ void load_half_h(Half<V2, true> &h, int x4, int s, int half,
+                                              unsigned long long pol) const {
+    const vec *p = base + site(s, x4) + (long long)half * 3 * VPQ * plane;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4 v = ld_vec<HINT>(p + (long long)c * plane, pol);
+      h.z[c][0] = make_float2(v.x, v.y);
+      h.z[c][1] = make_float2(v.z, v.w);
+    }
+  }
 };
 
 template <class P>
 __device__ __forceinline__ void store_spinor(typename P::vec *base, long long plane,
-                                             const Spinor<typename Pair<P>::type> &v) {
+                                             const SpinorP<P> &v) {
   constexpr int VPQ = 4 / P::R;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    quad_out(base + (long long)c * VPQ * plane, plane, v.up.re[c], v.up.im[c]);
-    quad_out(base + (long long)(3 + c) * VPQ * plane, plane, v.lo.re[c], v.lo.im[c]);
+    if constexpr (P::CPLX) {
+      __stcs(base + (long long)c * plane,
+             make_float4(v.up.z[c][0].x, v.up.z[c][0].y, v.up.z[c][1].x, v.up.z[c][1].y));
+      __stcs(base + (long long)(3 + c) * plane,
+             make_float4(v.lo.z[c][0].x, v.lo.z[c][0].y, v.lo.z[c][1].x, v.lo.z[c][1].y));
+    } else {
+      quad_out(base + (long long)c * VPQ * plane, plane, v.up.re[c], v.up.im[c]);
+      quad_out(base + (long long)(3 + c) * VPQ * plane, plane, v.lo.re[c], v.lo.im[c]);
+    }
   }
 }
 
@@ -410,27 +537,26 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
 // where W = U_mu(l4) (ADJ = false) or U_mu(l4)^+ (ADJ = true) and psi' is psi
 // itself (PHI = false) or phi = (b + cK) psi (PHI = true).
 template <class P, int MU, int S, bool ADJ, bool PHI, bool FIRST, int SPT, int HINT = HINT_NONE>
-__device__ __forceinline__ void hop_dir(Spinor<typename Pair<P>::type> (&acc)[SPT],
+__device__ __forceinline__ void hop_dir(SpinorP<P> (&acc)[SPT],
                                         const Field<P> &F, const typename P::vec *gauge,
                                         typename P::C lsign, int y4, int l4, int s0, int Ls,
                                         typename P::C b, typename P::C c, typename P::C mf) {
   using C = typename P::C;
-  using V2 = typename Pair<P>::type;
   C U[18];
   load_link<P>(U, gauge, MU, l4, lsign);
-  auto body = [&](int j, const Spinor<V2> &v) {
-    Half<V2> h, w;
+  auto body = [&](int j, const SpinorP<P> &v) {
+    HalfP<P> h, w;
     project<MU, S>(h, v.up, v.lo);
     su3_mul<ADJ>(w, U, h);
     reconstruct<MU, S, FIRST>(acc[j], w);
   };
-  if (PHI) {
+  if constexpr (PHI) {
     roll_5d<P, false, SPT>(F, y4, s0, Ls, b, c, mf, body);
   } else {
     const unsigned long long pol = l2_policy<HINT>();
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
-      Spinor<V2> v;
+      SpinorP<P> v;
       F.template load_half_h<HINT>(v.up, y4, s0 + j, 0, pol);
       F.template load_half_h<HINT>(v.lo, y4, s0 + j, 1, pol);
       body(j, v);
@@ -977,7 +1103,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   Fo.V4 = p.V4;
   Fo.Ls = p.Ls;
 
-  Spinor<V2> acc[SPT];
+  SpinorP<P> acc[SPT];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t smem_used = 0;
 
@@ -1019,7 +1145,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     }
   }
 
-  if (VAR == 6 || VAR == 7) {
+  if constexpr (VAR == 6 || VAR == 7) {
     // Rows path.  A tile is R = tx/32 whole x rows of one (z, t) plane; rows
     // y0-1 .. y0+R of the CTA's slices (one contiguous run per row in the
     // blocked layout) are bulk-copied into shared memory by one thread while
@@ -1128,23 +1254,34 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       }
     }
     if (RING) return;
-  } else if (VAR == 0 || VAR == 4 || VAR == 5) {
+  } else if constexpr (VAR == 0 || VAR == 4 || VAR == 5) {
     if (active) {
       const Hops H(p, x4);
       // t faces of a sub-lattice take their t-neighbours from the halos
+      // (spin-pair form only)
       const int Vf = p.L[0] * p.L[1] * p.L[2];
       const int ct = x4 / Vf;
       const long long hplane = (long long)Ls * Vf;
       const long long hrhs = hplane * (12 / P::R);
-      if (!CB && p.halo_up && ct == p.L[3] - 1)
-        halo_hop_up<P, SF, true, SPT>(acc, (const vec *)p.halo_up + rhs * hrhs, hplane, Vf,
-                                      x4 - ct * Vf, gauge, x4, (C)H.sign<3, true>(p), s0);
-      else
+      bool up_done = false, dn_done = false;
+      if constexpr (!P::CPLX) {
+        if (!CB && p.halo_up && ct == p.L[3] - 1) {
+          halo_hop_up<P, SF, true, SPT>(acc, (const vec *)p.halo_up + rhs * hrhs, hplane, Vf,
+                                        x4 - ct * Vf, gauge, x4, (C)H.sign<3, true>(p), s0);
+          up_done = true;
+        }
+      }
+      if (!up_done)
         hop_dir<P, 3, SF, false, PHI, true, SPT, VAR >= 4 ? HINT_KEEP : HINT_NONE>(
             acc, F, gauge, (C)H.sign<3, true>(p), fidx(H.nb<3, true>(p)), x4, s0, Ls, b, c, mf);
-      if (!CB && p.halo_dn && ct == 0)
-        halo_hop_down<P, SB, SPT>(acc, (const vec *)p.halo_dn + rhs * hrhs, hplane, Vf, x4, s0);
-      else
+      if constexpr (!P::CPLX) {
+        if (!CB && p.halo_dn && ct == 0) {
+          halo_hop_down<P, SB, SPT>(acc, (const vec *)p.halo_dn + rhs * hrhs, hplane, Vf, x4,
+                                    s0);
+          dn_done = true;
+        }
+      }
+      if (!dn_done)
         hop_dir<P, 3, SB, true, PHI, false, SPT, VAR >= 4 ? HINT_DROP : HINT_NONE>(
             acc, F, gauge, (C)H.sign<3, false>(p), fidx(H.nb<3, false>(p)), H.nb<3, false>(p),
             s0, Ls, b, c, mf);
@@ -1160,8 +1297,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       DW_HOP(0, false, SB, true);
 #undef DW_HOP
     }
-  } else if (VAR == 2 || VAR == 3) {
-    if (PHI) {  // the (b + cK) input combination keeps the VAR 0 path
+  } else if constexpr (VAR == 2 || VAR == 3) {
+    if constexpr (PHI) {  // the (b + cK) input combination keeps the VAR 0 path
       if (active) {
         hop_dir<P, 3, SF, false, PHI, true, SPT>(acc, F, gauge, (C)lsg[0], nb[0], x4, s0, Ls, b, c, mf);
         hop_dir<P, 3, SB, true, PHI, false, SPT>(acc, F, gauge, (C)lsg[1], nb[1], nb[1], s0, Ls, b, c, mf);
@@ -1175,7 +1312,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     } else if (active) {
       hop_prefetch<P, SPT, VAR == 2 ? 0 : 1, DAG>(acc, F, gauge, x4, nb, lsg, s0);
     }
-  } else {
+  } else if constexpr (VAR == 1) {
     StagedHop<P, OP, SPT> H;
     H.smem = smem_raw;
     H.T = tx * nchunk;
@@ -1184,17 +1321,17 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     smem_used = kStages * StageLayout<P, PHI, SPT>::stage_bytes(H.T);
   }
 
-  auto store = [&](int j, const Spinor<V2> &v) {
+  auto store = [&](int j, const SpinorP<P> &v) {
     store_spinor<P>(out + F.site(s0 + j, xf), kPlaneStride, v);
   };
   const V2 mhalf = bc<V2>((C)p.hscale);  // -1/2 of D_W, or the caller's factor
 
-  if (OP == OP_DHOP || OP == OP_DHOP_DAG) {
+  if constexpr (OP == OP_DHOP || OP == OP_DHOP_DAG) {
     if (active) {
 #pragma unroll
       for (int j = 0; j < SPT; ++j) store(j, acc[j]);
     }
-  } else if (OP == OP_D) {
+  } else if constexpr (OP == OP_D) {
     // out = alpha psi + beta K psi - 1/2 Dhop phi; optionally |out|^2 per CTA
     // (the CG's <p, D^+D p> = |D p|^2, fused here to save a pass over two fields)
     double nsq = 0.0;
@@ -1448,6 +1585,17 @@ int launch_variant(const DslashParams &p, int op, TileConfig cfg, cudaStream_t s
   return -2;
 }
 
+// Interleaved-complex FP32 entry points (layout ablation): Dhop and Dhop^+.
+template <int VAR>
+int launch_variant_cplx(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st) {
+  if (cfg.spt < 1 || p.Ls % cfg.spt) return -2;
+  switch (op) {
+    case OP_DHOP: return launch_spt<F32C, OP_DHOP, VAR>(p, cfg, st);
+    case OP_DHOP_DAG: return launch_spt<F32C, OP_DHOP_DAG, VAR>(p, cfg, st);
+  }
+  return -2;
+}
+
 // Checkerboard entry points (the D and D^+ forms; Dhop is D with b = 1,
 // c = 0, no local term and factor 1).
 template <class P, int VAR>
@@ -1491,6 +1639,15 @@ int max_threads_variant(int op, int spt) {
   int launch_dslash_cb_##PREC(const DslashParams &p, int op, TileConfig cfg,             \
                               cudaStream_t st) {                                         \
     return launch_variant_cb<PREC, VAR>(p, op, cfg, st);                                 \
+  }                                                                                      \
+  }
+
+// Interleaved-complex stencil of one variant.
+#define DW_DSLASH_CPLX_INSTANTIATE(VAR)                                                   \
+  namespace dw {                                                                         \
+  int launch_dslash_cplx_v##VAR(const DslashParams &p, int op, TileConfig cfg,           \
+                                cudaStream_t st) {                                       \
+    return launch_variant_cplx<VAR>(p, op, cfg, st);                                     \
   }                                                                                      \
   }
 

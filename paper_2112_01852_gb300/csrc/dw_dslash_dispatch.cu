@@ -42,6 +42,21 @@ int dslash_max_threads_F16_v6(int op, int spt);
 int launch_dslash_F16_v7(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F16_v7(int op, int spt);
 
+int launch_dslash_cplx_v4(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int launch_dslash_cplx_v5(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int launch_dslash_cplx_v6(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+int launch_dslash_cplx_v7(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
+
+int launch_dslash_cplx(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st) {
+  switch (cfg.variant) {
+    case 4: return launch_dslash_cplx_v4(p, op, cfg, st);
+    case 5: return launch_dslash_cplx_v5(p, op, cfg, st);
+    case 6: return launch_dslash_cplx_v6(p, op, cfg, st);
+    case 7: return launch_dslash_cplx_v7(p, op, cfg, st);
+  }
+  return -2;
+}
+
 int launch_dslash_cb_F64(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int launch_dslash_cb_F32(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int launch_dslash_cb_F16(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);

@@ -460,6 +460,8 @@ extern "C" int dw_apply_m5_eo(dw_lattice *lat, void *out, const void *in, const 
   if (out == in) return fail(DW_ERR_ARG, "out must not alias in");
   if (!mf) return fail(DW_ERR_ARG, "mf is NULL");
   if (nrhs < 1) return fail(DW_ERR_ARG, "nrhs must be >= 1");
+  if (lat->cplx && lat->prec == DW_F32)
+    return fail(DW_ERR_STATE, "interleaved-complex FP32 fields support Dhop and Dhop^+ only");
   return apply_m5(lat, lat->prec, out, in, mf, nrhs, inverse != 0, dag != 0,
                   (cudaStream_t)stream);
 }
@@ -474,6 +476,8 @@ extern "C" int dw_apply_schur(dw_lattice *lat, void *out, const void *in, const 
   if (!mf) return fail(DW_ERR_ARG, "mf is NULL");
   if (nrhs < 1) return fail(DW_ERR_ARG, "nrhs must be >= 1");
   if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  if (lat->cplx && lat->prec == DW_F32)
+    return fail(DW_ERR_STATE, "interleaved-complex FP32 fields support Dhop and Dhop^+ only");
   const size_t need = 2 * cb_field_bytes(lat, lat->prec, nrhs);
   if ((rc = ensure_buffer(&lat->scratch, &lat->scratch_bytes, need))) return rc;
   void *t1 = lat->scratch;

@@ -22,10 +22,17 @@ constexpr int kXposeTPB = 128;
 constexpr int kLaneStride = kSC * 24 + 1;  // doubles per site row of the staging array
 
 // internal real of the real part of canonical complex kk (spin*3 + colour);
-// the imaginary part is the internal real two further on
+// the imaginary part is the internal real P::IM further on.  Spin-pair quads
+// (Re j0, Re j1, Im j0, Im j1); interleaved-complex quads (CPLX, the layout
+// ablation) (Re j0, Im j0, Re j1, Im j1).
+template <class P>
 __device__ __forceinline__ int internal_re(int kk) {
   const int spin = kk / 3, c = kk % 3;
-  return (spin >> 1) * 12 + c * 4 + (spin & 1);
+  return (spin >> 1) * 12 + c * 4 + (spin & 1) * (P::CPLX ? 2 : 1);
+}
+template <class P>
+__host__ __device__ constexpr int im_offset() {
+  return P::CPLX ? 1 : 2;
 }
 
 template <class P>
@@ -46,9 +53,9 @@ __global__ void __launch_bounds__(kXposeTPB) pack_kernel(typename P::vec *dst,
     const int x4 = blk * 32 + lane;
     if (x4 >= V4) continue;
     const double2 v = __ldcs(src + ((long long)rhs * V5 + (long long)x4 * Ls + s0 + sl) * 12 + kk);
-    double *b = sm + lane * kLaneStride + sl * 24 + internal_re(kk);
+    double *b = sm + lane * kLaneStride + sl * 24 + internal_re<P>(kk);
     b[0] = v.x;
-    b[2] = v.y;
+    b[im_offset<P>()] = v.y;
   }
   __syncthreads();
   // staging -> internal: the chunk is one contiguous run of sc * NP * 32 vecs
@@ -93,9 +100,9 @@ __global__ void __launch_bounds__(kXposeTPB) unpack_kernel(double2 *dst,
     const int lane = o / (sc * 12), rem = o % (sc * 12), sl = rem / 12, kk = rem % 12;
     const int x4 = blk * 32 + lane;
     if (x4 >= V4) continue;
-    const double *b = sm + lane * kLaneStride + sl * 24 + internal_re(kk);
+    const double *b = sm + lane * kLaneStride + sl * 24 + internal_re<P>(kk);
     __stcs(dst + ((long long)rhs * V5 + (long long)x4 * Ls + s0 + sl) * 12 + kk,
-           make_double2(b[0], b[2]));
+           make_double2(b[0], b[im_offset<P>()]));
   }
 }
 
@@ -119,7 +126,8 @@ static int unpack_t(const FieldGeom &g, void *dst, const void *src, int nrhs, cu
 }
 
 int pack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int nrhs,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool cplx) {
+  if (cplx && prec == DW_F32) return pack_t<F32C>(g, dst, src, nrhs, st);
   switch (prec) {
     case DW_F64: return pack_t<F64>(g, dst, src, nrhs, st);
     case DW_F32: return pack_t<F32>(g, dst, src, nrhs, st);
@@ -129,7 +137,8 @@ int pack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int n
 }
 
 int unpack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int nrhs,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool cplx) {
+  if (cplx && prec == DW_F32) return unpack_t<F32C>(g, dst, src, nrhs, st);
   switch (prec) {
     case DW_F64: return unpack_t<F64>(g, dst, src, nrhs, st);
     case DW_F32: return unpack_t<F32>(g, dst, src, nrhs, st);

@@ -12,12 +12,13 @@ struct FieldGeom {
   long long V5() const { return (long long)V4 * Ls; }
 };
 
-// canonical complex128 (device) -> internal at `prec`
+// canonical complex128 (device) -> internal at `prec` (cplx: FP32 fields with
+// interleaved-complex quads)
 int pack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int nrhs,
-                 cudaStream_t st);
+                 cudaStream_t st, bool cplx = false);
 // internal at `prec` -> canonical complex128 (device)
 int unpack_fermion(const FieldGeom &g, int prec, void *dst, const void *src, int nrhs,
-                   cudaStream_t st);
+                   cudaStream_t st, bool cplx = false);
 // canonical gauge (device) -> internal links at F64, F32 and F16
 int load_gauge(const FieldGeom &g, const int bc[4], const void *U, void *const gauge[3],
                cudaStream_t st);

@@ -56,6 +56,7 @@ SYMBOLS = (
     "dw_halo_pack", "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
     "dw_unpack_fermion", "dw_last_error", "dw_fermion_bytes_eo", "dw_eo_split", "dw_eo_merge",
     "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo", "dw_get_tile", "dw_set_wait_polls",
+    "dw_set_complex_layout",
 )
 
 
@@ -110,6 +111,7 @@ def load_library():
             "dw_get_tile": (I, [P, I, I, I, IP, IP, IP, IP, IP]),
             "dw_device_status": (I, [P]),
             "dw_set_wait_polls": (I, [P, I]),
+            "dw_set_complex_layout": (I, [P, I]),
             "dw_fermion_bytes_eo": (S, [P, I, I]),
             "dw_eo_split": (I, [P, P, P, P, I, I, P]),
             "dw_eo_merge": (I, [P, P, P, P, I, I, P]),
@@ -236,6 +238,10 @@ def dw_tune(lat, op, nrhs, stream=0):
 def dw_device_status(lat):
     """Raises DWError (DW_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
     _check(load_library().dw_device_status(lat))
+
+
+def dw_set_complex_layout(lat, interleaved):
+    _check(load_library().dw_set_complex_layout(lat, int(interleaved)))
 
 
 def dw_set_wait_polls(lat, polls):
