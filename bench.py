@@ -527,6 +527,10 @@ def main():
     ap.add_argument("--layout", default="spin_pair", choices=["spin_pair", "complex"],
                     help="FP32 quad layout of the timed Dhop (complex: the interleaved-"
                          "complex layout of the ablation)")
+    ap.add_argument("--prec", default="f32", choices=["f32", "f16"],
+                    help="storage of the timed Dhop with --main-only (profiling runs)")
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="right-hand sides of the timed Dhop with --main-only (profiling runs)")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--cg-full", action="store_true",
                     help="also run the three CGs on the benchmark lattice (minutes)")
@@ -553,33 +557,37 @@ def main():
     from paper_2112_01852_gb300.lattice import Lattice
     cuda_build.build()
 
+    if not args.main_only and (args.prec != "f32" or args.nrhs != 1):
+        ap.error("--prec and --nrhs apply to --main-only runs")
+    NR = args.nrhs
+    prec = dw.DW_F16 if args.prec == "f16" else dw.DW_F32
     V4 = int(np.prod(DIMS))
     V5 = V4 * LS
     U = inputs.exp_su3_field(DIMS, seed=SEED)
-    psi = inputs.gaussian_fermion(DIMS, LS, 1, seed=SEED)
+    psi = inputs.gaussian_fermion(DIMS, LS, NR, seed=SEED)
 
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
-    lat = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32)
+    lat = Lattice(DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=prec)
     lat.load_gauge(U)
     if args.layout == "complex":
         dw.dw_set_complex_layout(lat.handle, 1)
     x = lat.pack(psi)
-    y = lat.empty(1)
+    y = lat.empty(NR)
     tiles = {}
     if args.tile:
         tv = [int(v) for v in args.tile.split(",")] + [0, 0, 1][len(args.tile.split(",")) - 2:]
         spt, tx, var, zb, sg = tv[:5]
-        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var, zblk=zb, sgrp=sg)
+        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var, nrhs=NR, zblk=zb, sgrp=sg)
         tiles[dw.DW_OP_DHOP] = (spt, tx, var, zb, sg)
     else:
-        tiles[dw.DW_OP_DHOP] = lat.tune(dw.DW_OP_DHOP, 1)
+        tiles[dw.DW_OP_DHOP] = lat.tune(dw.DW_OP_DHOP, NR)
     if not args.main_only:
         for op in (dw.DW_OP_D, dw.DW_OP_DDAG):
             tiles[op] = lat.tune(op, 1)
 
     def dhop():
-        dw.dw_apply_Dhop(lat.handle, y.data_ptr(), x.data_ptr(), 1, sh)
+        dw.dw_apply_Dhop(lat.handle, y.data_ptr(), x.data_ptr(), NR, sh)
 
     # warm-up and timed region (barrier + synchronize on both sides)
     for _ in range(args.warmup):
@@ -601,13 +609,13 @@ def main():
     torch.cuda.synchronize()
     _barrier(ws)
     clocks = sampler.stop()
-    ms, sites_per_s = aggregate(ws, e0.elapsed_time(e1) / args.steps, V5)
+    ms, sites_per_s = aggregate(ws, e0.elapsed_time(e1) / args.steps, V5 * NR)
     gflops = FLOP_DHOP * sites_per_s / 1e9
 
     # roofline of the Dhop kernel (one launch per step)
     peak, peak_kind = _peaks()
-    bps = bytes_per_site(4, LS)
-    alg_bytes = bps * V5
+    bps = bytes_per_site(2 if prec == dw.DW_F16 else 4, LS, NR)
+    alg_bytes = bps * V5 * NR
     achieved = alg_bytes / (ms * 1e-3) / 1e9
 
     line = {
@@ -619,13 +627,16 @@ def main():
                      "frac": achieved / peak,
                      "traffic": recorded_traffic(tiles[dw.DW_OP_DHOP], DIMS, LS),
                      "peak_source": peak_kind,
-                     "bytes_per_site": bps, "sites_per_launch": V5},
+                     "bytes_per_site": bps, "sites_per_launch": V5 * NR},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "tile": tiles[dw.DW_OP_DHOP],
     }
     if args.main_only or args.layout != "spin_pair":
         line["layout"] = args.layout
+        line["dtype"] = "f16" if prec == dw.DW_F16 else "f32"
+        line["config"]["nrhs"] = NR
+        line["config"]["prec"] = line["dtype"]
         if rank == 0:
             print(json.dumps(line), flush=True)
         lat.close()

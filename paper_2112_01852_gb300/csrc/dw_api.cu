@@ -113,6 +113,9 @@ bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (lat->cplx && prec == DW_F32 && !cplx_variant_ok(op, t.variant)) return false;
   if (t.tx < 32 || t.tx % 32) return false;
   if (t.variant < 0 || t.variant > kNumVariants - 1) return false;
+  if (t.variant == 8)  // the tensor-core hop: FP16 only, one tile shape
+    return prec == DW_F16 && !lat->cplx && tc_variant_ok(op, lat->dims[0], lat->Ls) &&
+           t.spt == 1 && t.tx == 32 && t.sgrp == 1 && t.zblk >= 1 && lat->dims[2] % t.zblk == 0;
   if (t.zblk < 1 || lat->dims[2] % t.zblk) return false;
   if (t.sgrp < 1 || (lat->Ls / t.spt) % t.sgrp || (op == OP_DDAG && t.sgrp != 1)) return false;
   if ((t.variant == 6 || t.variant == 7) &&
@@ -389,8 +392,9 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d sgrp=%d for Ls=%d Lz=%d (slices "
-                "per thread must divide Ls, tx a multiple of 32, variant 0..7 (6, 7: Lx = 32 and "
-                "Dhop only), zblk dividing Lz, sgrp dividing Ls/spt and 1 for D^+, CTA within "
+                "per thread must divide Ls, tx a multiple of 32, variant 0..8 (6, 7: Lx = 32 and "
+                "Dhop only; 8: FP16 Dhop, Lx even, Ls a multiple of 4 up to 16, spt 1, tx 32, "
+                "sgrp 1), zblk dividing Lz, sgrp dividing Ls/spt and 1 for D^+, CTA within "
                 "the kernel's limits)",
                 spt, tx, variant, zblk, sgrp, lat->Ls, lat->dims[2]);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;

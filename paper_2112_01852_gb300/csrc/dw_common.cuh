@@ -189,7 +189,7 @@ struct TileConfig {
   int zblk;     // z-blocks of the CTA traversal order (divides Lz)
   int sgrp;     // CTAs sharing one tile of sites, each with Ls / (spt sgrp) thread rows
 };
-constexpr int kNumVariants = 8;
+constexpr int kNumVariants = 9;
 
 // Variants 6 and 7 stage rows in shared memory: they need Lx = 32 (a 32-site
 // block is one x row), tiles of whole rows that tile the (x, y) plane, the
@@ -209,6 +209,13 @@ inline size_t rows_smem_bytes(int tx, int nsl, int prec) {
 // that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA
 // launch error.
 int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
+// Variant 8: FP16 hopping term with the SU(3) x half-spinor products on the
+// tensor cores (dw_dslash_tc.cu): Dhop / Dhop^+, Lx even, Ls a multiple of 4 up
+// to 16; one tile shape (spt 1, tx 32, sgrp 1, zblk unused).
+inline bool tc_variant_ok(int op, int Lx, int Ls) {
+  return (op == OP_DHOP || op == OP_DHOP_DAG) && Lx % 2 == 0 && Ls % 4 == 0 && Ls <= 16;
+}
+int launch_dslash_tc_F16(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 // Stencil on interleaved-complex FP32 fields (layout ablation): Dhop / Dhop^+
 // with variants 4-7 only; same return codes.
 int launch_dslash_cplx(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);

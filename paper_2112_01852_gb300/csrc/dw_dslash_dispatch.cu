@@ -101,6 +101,7 @@ int launch_dslash(const DslashParams &p, int prec, int op, TileConfig cfg, cudaS
         case 5: return launch_dslash_F16_v5(p, op, cfg, st);
         case 6: return launch_dslash_F16_v6(p, op, cfg, st);
         case 7: return launch_dslash_F16_v7(p, op, cfg, st);
+        case 8: return launch_dslash_tc_F16(p, op, cfg, st);
         default: return -2;
       }
   }
