@@ -351,6 +351,37 @@ int dw_set_wait_polls(dw_lattice *lat, int polls);
 size_t dw_halo_bytes(const dw_lattice *lat, int prec, int nrhs);
 int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, int nrhs,
                  int dag, void *stream);
+/*
+ * The same for any stencil operator op = DW_OP_DHOP, DW_OP_DHOP_DAG, DW_OP_D or
+ * DW_OP_DDAG, for ranks in separate processes (the exchange of the paper's MPI
+ * runs, Sec. 4.2): D's hopping term acts on phi = (b + cK) psi, so its faces are
+ * those of phi (formed with the masses mf[nrhs], HOST, with the arithmetic of the
+ * undecomposed kernel); D^+'s are those of Dhop^+ (its 5D part follows the hop
+ * and is local).  dw_apply_op_halo applies op on the sub-lattice with the
+ * received faces (mf as for dw_apply_D; NULL for the hopping terms); the
+ * stitched result equals the undecomposed operator with a variant-0 tile bit for
+ * bit.  Both return DW_ERR_STATE on an interleaved-complex lattice.
+ */
+int dw_halo_pack_op(dw_lattice *lat, int op, void *send_dn, void *send_up, const void *in,
+                    const double *mf, int nrhs, void *stream);
+int dw_apply_op_halo(dw_lattice *lat, int op, void *out, const void *in, const void *recv_up,
+                     const void *recv_dn, const double *mf, int nrhs, void *stream);
+
+/*
+ * Level-1 field operations on DEVICE fields in the internal layout at precision
+ * prec (nrhs each), for solvers driven from the host, e.g. a CG whose global
+ * sums are completed across ranks.  The paper gives no solver; these are the
+ * vector steps of textbook CG.
+ * dw_field_redot: out[r] (HOST) = Re <a_r, b_r> over the lattice's sites, summed
+ *   in FP64 in a fixed order (deterministic); synchronises `stream`.
+ * dw_field_axpby: y_r = a[r] x_r + b[r] y_r (a, b HOST arrays of nrhs), in FP64
+ *   arithmetic when prec is DW_F64, FP32 otherwise; y may alias x.
+ * Return DW_OK, DW_ERR_ARG or DW_ERR_STATE (interleaved-complex FP32 fields).
+ */
+int dw_field_redot(dw_lattice *lat, int prec, const void *a, const void *b, int nrhs,
+                   double *out, void *stream);
+int dw_field_axpby(dw_lattice *lat, int prec, void *y, const double *a, const void *x,
+                   const double *b, int nrhs, void *stream);
 int dw_apply_Dhop_halo(dw_lattice *lat, void *out, const void *in, const void *recv_up,
                        const void *recv_dn, int nrhs, int dag, void *stream);
 

@@ -475,51 +475,96 @@ size_t dw_halo_bytes(const dw_lattice *lat, int prec, int nrhs) {
   return halo_bytes(lat, prec, nrhs);
 }
 
-int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, int nrhs,
-                 int dag, void *stream) {
-  clear_error();
+}  // extern "C"
+
+namespace dw {
+
+// Faces of stencil operator `op` (OpKind) over nrhs RHS, in launches of at most
+// kMaxRhsPerLaunch RHS (masses by value).
+static int halo_pack_op(dw_lattice *lat, int op, void *send_dn, void *send_up, const void *in,
+                        const double *mf, int nrhs, cudaStream_t st) {
+  const size_t rhs_bytes = field_bytes(lat, lat->prec, 1);
+  const size_t hrhs_bytes = halo_bytes(lat, lat->prec, 1);
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
+    const int n = (nrhs - r0) < kMaxRhsPerLaunch ? (nrhs - r0) : kMaxRhsPerLaunch;
+    DslashParams p;
+    memset(&p, 0, sizeof(p));
+    p.wait_polls = -1;
+    p.in = (const char *)in + (size_t)r0 * rhs_bytes;
+    p.gauge = lat->gauge[lat->prec];
+    for (int m = 0; m < 4; ++m) p.bc[m] = lat->bc[m];
+    for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
+    p.V4 = (int)lat->V4;
+    p.Ls = lat->Ls;
+    p.plane = kPlaneStride;
+    p.rhs_stride = lat->V4p * lat->Ls * (24 / prec_reals_per_vec(lat->prec));
+    p.nrhs = n;
+    p.b = lat->b;
+    p.c = lat->c;
+    for (int r = 0; r < n; ++r) p.mf[r] = mf ? mf[r0 + r] : 0.0;
+    void *dn = (char *)send_dn + (size_t)r0 * hrhs_bytes;
+    void *up = (char *)send_up + (size_t)r0 * hrhs_bytes;
+    int rc;
+    switch (lat->prec) {
+      case DW_F64: rc = launch_halo_pack_F64(p, dn, up, op, st); break;
+      case DW_F32: rc = launch_halo_pack_F32(p, dn, up, op, st); break;
+      default: rc = launch_halo_pack_F16(p, dn, up, op, st); break;
+    }
+    if (rc) return cuda_fail(cudaGetLastError(), "halo pack launch");
+  }
+  return DW_OK;
+}
+
+static int check_halo(dw_lattice *lat, int op, const double *mf) {
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (op < DW_OP_DHOP || op > DW_OP_DDAG) return fail(DW_ERR_ARG, "unknown operator %d", op);
+  if (op >= DW_OP_D && !mf) return fail(DW_ERR_ARG, "mf is NULL");
+  if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
+  if (lat->cplx && lat->prec == DW_F32)
+    return fail(DW_ERR_STATE, "the decomposed operators need the spin-pair layout");
+  return DW_OK;
+}
+
+}  // namespace dw
+
+extern "C" {
+
+int dw_halo_pack_op(dw_lattice *lat, int op, void *send_dn, void *send_up, const void *in,
+                    const double *mf, int nrhs, void *stream) {
+  clear_error();
+  int rc = check_halo(lat, op, mf);
+  if (rc) return rc;
   if (!send_dn || !send_up || !in) return fail(DW_ERR_ARG, "buffer pointer is NULL");
   if (!aligned16(send_dn) || !aligned16(send_up) || !aligned16(in))
     return fail(DW_ERR_ARG, "buffers must be 16-byte aligned");
   if (nrhs < 1 || nrhs > 65535) return fail(DW_ERR_ARG, "nrhs out of range");
-  if (!lat->gauge_loaded) return fail(DW_ERR_STATE, "dw_load_gauge has not been called");
-  if (lat->cplx && lat->prec == DW_F32)
-    return fail(DW_ERR_STATE, "interleaved-complex FP32 fields support Dhop and Dhop^+ only");
-  DslashParams p;
-  memset(&p, 0, sizeof(p));
-  p.wait_polls = -1;
-  p.in = in;
-  p.gauge = lat->gauge[lat->prec];
-  for (int m = 0; m < 4; ++m) p.bc[m] = lat->bc[m];
-  for (int m = 0; m < 4; ++m) p.L[m] = lat->dims[m];
-  p.V4 = (int)lat->V4;
-  p.Ls = lat->Ls;
-  p.plane = kPlaneStride;
-  p.rhs_stride = lat->V4p * lat->Ls * (24 / prec_reals_per_vec(lat->prec));
-  p.nrhs = nrhs;
-  int rc;
-  switch (lat->prec) {
-    case DW_F64: rc = launch_halo_pack_F64(p, send_dn, send_up, dag, (cudaStream_t)stream); break;
-    case DW_F32: rc = launch_halo_pack_F32(p, send_dn, send_up, dag, (cudaStream_t)stream); break;
-    default: rc = launch_halo_pack_F16(p, send_dn, send_up, dag, (cudaStream_t)stream); break;
-  }
-  if (rc) return cuda_fail(cudaGetLastError(), "halo pack launch");
-  return DW_OK;
+  return halo_pack_op(lat, op, send_dn, send_up, in, mf, nrhs, (cudaStream_t)stream);
+}
+
+int dw_halo_pack(dw_lattice *lat, void *send_dn, void *send_up, const void *in, int nrhs,
+                 int dag, void *stream) {
+  return dw_halo_pack_op(lat, dag ? DW_OP_DHOP_DAG : DW_OP_DHOP, send_dn, send_up, in, nullptr,
+                         nrhs, stream);
+}
+
+int dw_apply_op_halo(dw_lattice *lat, int op, void *out, const void *in, const void *recv_up,
+                     const void *recv_dn, const double *mf, int nrhs, void *stream) {
+  clear_error();
+  int rc = check_halo(lat, op, mf);
+  if (rc) return rc;
+  if ((rc = check_apply(lat, out, in, mf, nrhs, op >= DW_OP_D))) return rc;
+  if (!recv_up || !recv_dn) return fail(DW_ERR_ARG, "halo pointer is NULL");
+  if (!aligned16(recv_up) || !aligned16(recv_dn))
+    return fail(DW_ERR_ARG, "halos must be 16-byte aligned");
+  TileConfig t = default_tile(lat, lat->prec, op, nrhs);  // the halo path is variant 0
+  return run_dslash(lat, lat->prec, op, out, in, op >= DW_OP_D ? mf : nullptr, nrhs,
+                    (cudaStream_t)stream, &t, nullptr, 0, recv_up, recv_dn);
 }
 
 int dw_apply_Dhop_halo(dw_lattice *lat, void *out, const void *in, const void *recv_up,
                        const void *recv_dn, int nrhs, int dag, void *stream) {
-  clear_error();
-  int rc = check_apply(lat, out, in, nullptr, nrhs, false);
-  if (rc) return rc;
-  if (!recv_up || !recv_dn) return fail(DW_ERR_ARG, "halo pointer is NULL");
-  if (!aligned16(recv_up) || !aligned16(recv_dn))
-    return fail(DW_ERR_ARG, "halos must be 16-byte aligned");
-  const int op = dag ? OP_DHOP_DAG : OP_DHOP;
-  TileConfig t = default_tile(lat, lat->prec, op, nrhs);  // the halo path is variant 0
-  return run_dslash(lat, lat->prec, op, out, in, nullptr, nrhs, (cudaStream_t)stream, &t,
-                    nullptr, 0, recv_up, recv_dn);
+  return dw_apply_op_halo(lat, dag ? DW_OP_DHOP_DAG : DW_OP_DHOP, out, in, recv_up, recv_dn,
+                          nullptr, nrhs, stream);
 }
 
 size_t dw_fermion_bytes(const dw_lattice *lat, int prec, int nrhs) {

@@ -428,6 +428,28 @@ __global__ void cg_clear_update_kernel(CGState *st, int nrhs) {
   st[rhs].run = st[rhs].active;
 }
 
+// y = a[rhs] x + b[rhs] y (coefficients by value, at most kMaxRhsPerLaunch RHS)
+template <class PY, class PX>
+__global__ void __launch_bounds__(kBlasThreads)
+    axpby_kernel(void *y, const void *x, SlotGeom L, size_t by, size_t bx, AxpbyCoefs cf) {
+  const int rhs = blockIdx.y;
+  using A = typename Arith<PY, PX>::T;
+  void *py = RHS_PTR(char *, y, rhs, by);
+  const void *px = RHS_PTR(const char *, x, rhs, bx);
+  const A a = (A)cf.a[rhs], b = (A)cf.b[rhs];
+  SLOT_LOOP(i) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      A xv[4], yv[4];
+      ld4<PX>(xv, px, q, i);
+      ld4<PY>(yv, py, q, i);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) yv[k] = a * xv[k] + b * yv[k];
+      st4<PY>(py, q, i, yv);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 
@@ -463,6 +485,16 @@ int blas_redot(const BlasCtx &c, int pa, const void *a, int pb, const void *b, d
   DISPATCH_PREC(pa, PA, DISPATCH_PREC(pb, PB,
       redot_kernel<PA, PB><<<grid, kBlasThreads, 0, s>>>(a, b, c.geom, rbytes(pa, c.geom),
                                                          rbytes(pb, c.geom), partial, st)));
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int blas_axpby(const BlasCtx &c, int py, void *y, int px, const void *x, const AxpbyCoefs &cf,
+               cudaStream_t s) {
+  if (c.nrhs > kMaxRhsPerLaunch) return -2;
+  dim3 grid(c.nblk, c.nrhs);
+  DISPATCH_PREC(py, PY, DISPATCH_PREC(px, PX,
+      axpby_kernel<PY, PX><<<grid, kBlasThreads, 0, s>>>(y, x, c.geom, rbytes(py, c.geom),
+                                                         rbytes(px, c.geom), cf)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -50,6 +50,13 @@ struct BlasCtx {
 
 int blas_redot(const BlasCtx &c, int pa, const void *a, int pb, const void *b, double *partial,
                const CGState *st, cudaStream_t s);
+// y = a[r] x + b[r] y for each RHS r (c.nrhs <= kMaxRhsPerLaunch)
+struct AxpbyCoefs {
+  double a[kMaxRhsPerLaunch];
+  double b[kMaxRhsPerLaunch];
+};
+int blas_axpby(const BlasCtx &c, int py, void *y, int px, const void *x, const AxpbyCoefs &cf,
+               cudaStream_t s);
 int blas_finalize_sum(const BlasCtx &c, const double *partial, double *out, cudaStream_t s);
 int cg_residual(const BlasCtx &c, double *r, const double *b, const double *Ax, double *partial,
                 const CGState *st, cudaStream_t s);

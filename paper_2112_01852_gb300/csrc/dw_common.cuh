@@ -226,12 +226,13 @@ inline bool cplx_variant_ok(int op, int variant) {
 int launch_dslash_cb(const DslashParams &p, int prec, int op, TileConfig cfg, cudaStream_t st);
 // Largest CTA the stencil kernel (op, spt, variant) can launch (0: none).
 int dslash_max_threads(int prec, int op, int spt, int variant);
-// Face halves of a t-decomposed sub-lattice (see dw_halo_pack).
-int launch_halo_pack_F64(const DslashParams &p, void *send_dn, void *send_up, int dag,
+// Face halves of a t-decomposed sub-lattice for stencil operator `op` (an
+// OpKind; see dw_halo_pack_op).
+int launch_halo_pack_F64(const DslashParams &p, void *send_dn, void *send_up, int op,
                          cudaStream_t st);
-int launch_halo_pack_F32(const DslashParams &p, void *send_dn, void *send_up, int dag,
+int launch_halo_pack_F32(const DslashParams &p, void *send_dn, void *send_up, int op,
                          cudaStream_t st);
-int launch_halo_pack_F16(const DslashParams &p, void *send_dn, void *send_up, int dag,
+int launch_halo_pack_F16(const DslashParams &p, void *send_dn, void *send_up, int op,
                          cudaStream_t st);
 
 struct CGWork;

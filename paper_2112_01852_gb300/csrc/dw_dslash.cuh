@@ -913,13 +913,41 @@ __device__ __forceinline__ void halo_hop_down(Spinor<typename Pair<P>::type> (&a
 
 // Face halves a rank sends: to the rank below, the forward-hop projection of
 // its first t slice; to the rank above, U_t^+ times the backward-hop
-// projection of its last t slice.  One thread per (face site, s) of one RHS.
-template <class P, bool DAG>
+// projection of its last t slice.  PHI: the hop acts on phi = (b + cK) psi (the
+// operator D), formed at the face slices with the same arithmetic as roll_5d,
+// so the receiver's sums equal the undecomposed kernel's bit for bit.  One
+// thread per (face site, s) of one RHS.
+template <class P, bool PHI>
+__device__ __forceinline__ void face_spinor(Spinor<typename Pair<P>::type> &v, const Field<P> &F,
+                                            int x4, int s, int Ls, typename P::C b,
+                                            typename P::C c, typename P::C mf) {
+  using C = typename P::C;
+  using V2 = typename Pair<P>::type;
+  if (!PHI) {
+    F.load_half(v.up, x4, s, 0);
+    F.load_half(v.lo, x4, s, 1);
+    return;
+  }
+  // phi_s: upper = b u_s + c fp u_{s-1}, lower = b l_s + c fn l_{s+1}
+  Half<V2> u, up, l, ln;
+  const int sp = s == 0 ? Ls - 1 : s - 1;
+  const int sn = s == Ls - 1 ? 0 : s + 1;
+  const C fp = s == 0 ? -mf : C(1);
+  const C fn = s == Ls - 1 ? -mf : C(1);
+  F.load_half(u, x4, s, 0);
+  F.load_half(up, x4, sp, 0);
+  F.load_half(l, x4, s, 1);
+  F.load_half(ln, x4, sn, 1);
+  half_axpby(v.up, bc<V2>(b), u, bc<V2>(c * fp), up);
+  half_axpby(v.lo, bc<V2>(b), l, bc<V2>(c * fn), ln);
+}
+
+template <class P, bool DAG, bool PHI>
 __global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send_up,
                                  const typename P::vec *in, const typename P::vec *gauge,
                                  int bct, int V4, int Vf, int Lt, int Ls,
                                  long long plane, long long rhs_stride, long long hplane,
-                                 long long hrhs) {
+                                 long long hrhs, const DslashParams p) {
   using C = typename P::C;
   using V2 = typename Pair<P>::type;
   constexpr int SF = DAG ? 1 : -1;
@@ -935,21 +963,21 @@ __global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send
   F.V4 = V4;
   F.Ls = Ls;
   (void)plane;
+  const C b = (C)p.b, c = (C)p.c, mf = PHI ? (C)p.mf[rhs] : C(0);
   {  // first slice -> rank below
     Spinor<V2> v;
-    F.load_half(v.up, face, s, 0);
-    F.load_half(v.lo, face, s, 1);
+    face_spinor<P, PHI>(v, F, face, s, Ls, b, c, mf);
     Half<V2> h;
     project<3, SF>(h, v.up, v.lo);
     typename P::vec *o = send_dn + (long long)rhs * hrhs + (long long)s * Vf + face;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) quad_out(o + (long long)c * VPQ * hplane, hplane, h.re[c], h.im[c]);
+    for (int cc = 0; cc < 3; ++cc)
+      quad_out(o + (long long)cc * VPQ * hplane, hplane, h.re[cc], h.im[cc]);
   }
   {  // last slice -> rank above
     const int x4 = face + (Lt - 1) * Vf;
     Spinor<V2> v;
-    F.load_half(v.up, x4, s, 0);
-    F.load_half(v.lo, x4, s, 1);
+    face_spinor<P, PHI>(v, F, x4, s, Ls, b, c, mf);
     Half<V2> h, w;
     project<3, SB>(h, v.up, v.lo);
     C U[18];
@@ -957,12 +985,14 @@ __global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send
     su3_mul<true>(w, U, h);
     typename P::vec *o = send_up + (long long)rhs * hrhs + (long long)s * Vf + face;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) quad_out(o + (long long)c * VPQ * hplane, hplane, w.re[c], w.im[c]);
+    for (int cc = 0; cc < 3; ++cc)
+      quad_out(o + (long long)cc * VPQ * hplane, hplane, w.re[cc], w.im[cc]);
   }
 }
 
+// op: OP_DHOP / OP_DHOP_DAG / OP_D (faces of phi) / OP_DDAG (faces of Dhop^+).
 template <class P>
-int launch_halo_pack_impl(const DslashParams &p, void *send_dn, void *send_up, int dag,
+int launch_halo_pack_impl(const DslashParams &p, void *send_dn, void *send_up, int op,
                           cudaStream_t st) {
   const int Vf = p.L[0] * p.L[1] * p.L[2];
   const long long hplane = (long long)p.Ls * Vf;
@@ -970,14 +1000,18 @@ int launch_halo_pack_impl(const DslashParams &p, void *send_dn, void *send_up, i
   const int tpb = 128;
   dim3 grid((unsigned)(((long long)Vf * p.Ls + tpb - 1) / tpb), p.nrhs);
   using vec = typename P::vec;
-  if (dag)
-    halo_pack_kernel<P, true><<<grid, tpb, 0, st>>>(
-        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gauge, p.bc[3], p.V4,
-        Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
-  else
-    halo_pack_kernel<P, false><<<grid, tpb, 0, st>>>(
-        (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gauge, p.bc[3], p.V4,
-        Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs);
+#define DW_HALO_LAUNCH(DAG, PHI)                                                            \
+  halo_pack_kernel<P, DAG, PHI><<<grid, tpb, 0, st>>>(                                      \
+      (vec *)send_dn, (vec *)send_up, (const vec *)p.in, (const vec *)p.gauge, p.bc[3], p.V4, \
+      Vf, p.L[3], p.Ls, p.plane, p.rhs_stride, hplane, hrhs, p)
+  switch (op) {
+    case OP_DHOP: DW_HALO_LAUNCH(false, false); break;
+    case OP_DHOP_DAG: DW_HALO_LAUNCH(true, false); break;
+    case OP_D: DW_HALO_LAUNCH(false, true); break;
+    case OP_DDAG: DW_HALO_LAUNCH(true, false); break;
+    default: return -2;
+  }
+#undef DW_HALO_LAUNCH
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -1654,8 +1688,8 @@ int max_threads_variant(int op, int spt) {
 // Face packing for the t decomposition, one translation unit per precision.
 #define DW_HALO_INSTANTIATE(PREC)                                                         \
   namespace dw {                                                                         \
-  int launch_halo_pack_##PREC(const DslashParams &p, void *send_dn, void *send_up, int dag, \
+  int launch_halo_pack_##PREC(const DslashParams &p, void *send_dn, void *send_up, int op,  \
                               cudaStream_t st) {                                         \
-    return launch_halo_pack_impl<PREC>(p, send_dn, send_up, dag, st);                    \
+    return launch_halo_pack_impl<PREC>(p, send_dn, send_up, op, st);                     \
   }                                                                                      \
   }

@@ -56,7 +56,8 @@ SYMBOLS = (
     "dw_halo_pack", "dw_apply_Dhop_halo", "dw_fermion_bytes", "dw_pack_fermion",
     "dw_unpack_fermion", "dw_last_error", "dw_fermion_bytes_eo", "dw_eo_split", "dw_eo_merge",
     "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo", "dw_get_tile", "dw_set_wait_polls",
-    "dw_set_complex_layout",
+    "dw_set_complex_layout", "dw_halo_pack_op", "dw_apply_op_halo", "dw_field_redot",
+    "dw_field_axpby",
 )
 
 
@@ -120,6 +121,10 @@ def load_library():
             "dw_solve_eo": (I, [P, P, P, DP, I, D, I, I, ctypes.POINTER(dw_cg_stats), P]),
             "dw_halo_bytes": (S, [P, I, I]),
             "dw_halo_pack": (I, [P, P, P, P, I, I, P]),
+            "dw_halo_pack_op": (I, [P, I, P, P, P, DP, I, P]),
+            "dw_apply_op_halo": (I, [P, I, P, P, P, P, DP, I, P]),
+            "dw_field_redot": (I, [P, I, P, P, I, DP, P]),
+            "dw_field_axpby": (I, [P, I, P, DP, P, DP, I, P]),
             "dw_apply_Dhop_halo": (I, [P, P, P, P, P, I, I, P]),
             "dw_fermion_bytes": (S, [P, I, I]),
             "dw_pack_fermion": (I, [P, P, I, P, I, P]),
@@ -289,6 +294,31 @@ def dw_halo_pack(lat, send_dn, send_up, inp, nrhs, dag=0, stream=0):
 def dw_apply_Dhop_halo(lat, out, inp, recv_up, recv_dn, nrhs, dag=0, stream=0):
     _check(load_library().dw_apply_Dhop_halo(lat, out, inp, recv_up, recv_dn, int(nrhs),
                                              int(dag), stream))
+
+
+def dw_halo_pack_op(lat, op, send_dn, send_up, inp, mf, nrhs, stream=0):
+    _check(load_library().dw_halo_pack_op(lat, int(op), send_dn, send_up, inp,
+                                          None if mf is None else _doubles(mf), int(nrhs),
+                                          stream))
+
+
+def dw_apply_op_halo(lat, op, out, inp, recv_up, recv_dn, mf, nrhs, stream=0):
+    _check(load_library().dw_apply_op_halo(lat, int(op), out, inp, recv_up, recv_dn,
+                                           None if mf is None else _doubles(mf), int(nrhs),
+                                           stream))
+
+
+def dw_field_redot(lat, prec, a, b, nrhs, stream=0):
+    """Re <a_r, b_r> per right-hand side (FP64, host list)."""
+    out = (ctypes.c_double * int(nrhs))()
+    _check(load_library().dw_field_redot(lat, int(prec), a, b, int(nrhs), out, stream))
+    return [float(v) for v in out]
+
+
+def dw_field_axpby(lat, prec, y, a, x, b, nrhs, stream=0):
+    """y_r = a[r] x_r + b[r] y_r."""
+    _check(load_library().dw_field_axpby(lat, int(prec), y, _doubles(a), x, _doubles(b),
+                                         int(nrhs), stream))
 
 
 def dw_fermion_bytes(lat, prec, nrhs):

@@ -42,3 +42,91 @@ def test_two_ranks_gloo_max_time_and_total_rate():
         ms, rate = out[rank]
         assert ms == pytest.approx(4.0)
         assert rate == pytest.approx(2 * 1000 / 4.0e-3)
+
+
+# ---------------------------------------------------------------------------
+# The multi-rank data plane's host logic (paper_2112_01852_gb300.dist) on two
+# gloo ranks: the t-ring exchange delivers each face to the right neighbour,
+# the all-reduce sums over ranks, and the distributed CG, run over a stand-in
+# vector space whose operator needs the same face exchange (a massive
+# Laplacian on a periodic 1D lattice split into slabs, CPU tensors), reaches
+# the dense solution.
+
+
+def _ring_ops(comm, n_loc, nrhs, m2):
+    import torch
+
+    class RingOps:
+        def new(self):
+            return torch.zeros(nrhs, n_loc, dtype=torch.float64)
+
+        def apply(self, out, inp):
+            # faces: the first site goes to the rank below, the last to the rank above
+            send_dn = inp[:, :1].contiguous()
+            send_up = inp[:, -1:].contiguous()
+            recv_up, recv_dn = torch.empty_like(send_dn), torch.empty_like(send_up)
+            comm.exchange(send_dn, send_up, recv_up, recv_dn)
+            right = torch.cat([inp[:, 1:], recv_up], dim=1)
+            left = torch.cat([recv_dn, inp[:, :-1]], dim=1)
+            out.copy_((m2 + 2.0) * inp - left - right)
+
+        def dot(self, a, b):
+            return comm.allreduce((a * b).sum(dim=1).tolist())
+
+        def axpby(self, y, a, x, b):
+            y.copy_(torch.tensor(a)[:, None] * x + torch.tensor(b)[:, None] * y)
+
+    return RingOps()
+
+
+def _dist_worker(rank, world, port, out):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+    from paper_2112_01852_gb300 import dist
+    tdist.init_process_group("gloo", rank=rank, world_size=world,
+                             init_method="tcp://127.0.0.1:%d" % port)
+    comm = dist.TComm()
+    assert (comm.rank, comm.size, comm.up, comm.dn) == (rank, world, (rank + 1) % world,
+                                                         (rank - 1) % world)
+    send_dn = torch.full((3,), 10.0 * rank + 1.0)
+    send_up = torch.full((3,), 10.0 * rank + 2.0)
+    recv_up, recv_dn = torch.empty(3), torch.empty(3)
+    comm.exchange(send_dn, send_up, recv_up, recv_dn)
+    exch = (float(recv_up[0]), float(recv_dn[0]))
+    red = comm.allreduce([rank + 1.0, 2.0 ** rank])
+    # distributed CG on the slab-decomposed ring
+    n_loc, nrhs, m2 = 8, 2, 0.3
+    N = n_loc * world
+    rng = np.random.default_rng(7)
+    bglob = rng.standard_normal((nrhs, N))
+    ops = _ring_ops(comm, n_loc, nrhs, m2)
+    b = torch.from_numpy(bglob[:, rank * n_loc:(rank + 1) * n_loc].copy())
+    x = ops.new()
+    conv, iters, res = dist.cg(ops, x, b, nrhs, 1e-12, 500)
+    xs = comm.allgather_numpy(x.numpy())
+    out[rank] = (exch, red, conv, iters, res, np.concatenate(xs, axis=1) if world > 1 else xs)
+    tdist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_data_plane_and_distributed_cg(world):
+    import numpy as np
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_dist_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    n_loc, nrhs, m2 = 8, 2, 0.3
+    N = n_loc * world
+    A = (m2 + 2.0) * np.eye(N) - np.roll(np.eye(N), 1, axis=1) - np.roll(np.eye(N), -1, axis=1)
+    bglob = np.random.default_rng(7).standard_normal((nrhs, N))
+    want = np.linalg.solve(A, bglob.T).T
+    for rank in range(world):
+        exch, red, conv, iters, res, x = out[rank]
+        up, dn = (rank + 1) % world, (rank - 1) % world
+        # recv_up is the rank above's send_dn, recv_dn the rank below's send_up
+        assert exch == (10.0 * up + 1.0, 10.0 * dn + 2.0)
+        assert red == [sum(range(1, world + 1)) * 1.0, float(2 ** world - 1)]
+        assert all(conv) and max(res) <= 1e-12 and 0 < iters <= 500
+        assert np.allclose(x, want, rtol=0, atol=1e-10)
