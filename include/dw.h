@@ -249,13 +249,16 @@ int dw_solve_eo(dw_lattice *lat, void *x, const void *eta, const double *mf, int
  * 2, 3 = loaded one (direction, slice) step ahead into registers, visiting
  * t,z,y,x (2) or x,y,z,t (3); 5 = variant 0 with L2 eviction hints: t+
  * neighbours kept, t- neighbours evicted first; 4 = variant 5 with at most
- * 128 registers per thread; 6 = variant 4 with the tile's x rows and their two
- * y-neighbour rows bulk-copied into shared memory, the x and y hops read there
- * (needs Lx = 32, tx dividing Lx*Ly, DW_OP_DHOP / DW_OP_DHOP_DAG only; its
- * bounded wait reports through dw_device_status); 7 = variant 6 with one CTA
- * walking all tiles of its (z, t) plane in y, the rows kept in a ring so that
- * each row is copied once per plane (same conditions); FP64 builds 0 and 2
- * only), zblk, the
+ * 128 registers per thread; 6 = variant 4 with the tile's 32-site blocks of
+ * the (x, y) plane and the block on either side bulk-copied into shared memory,
+ * the x and y hops read there (needs Lx <= 32, Lx*Ly a multiple of 32, tx
+ * dividing Lx*Ly, DW_OP_DHOP / DW_OP_DHOP_DAG only; its bounded wait reports
+ * through dw_device_status); 7 = variant 6 with one CTA walking all tiles of
+ * its (z, t) plane, the blocks kept in a ring so that each is copied once per
+ * plane (same conditions); 8 = FP16 storage only: the hopping term with its
+ * SU(3) x half-spinor products on the tensor cores (mma.sync m16n8k16), Lx
+ * even, Ls a multiple of 4 up to 16, the one tile spt 1, tx 32, sgrp 1; FP64
+ * builds 0 and 2 only; interleaved-complex FP32 lattices 4-7 only), zblk, the
  * number of z-blocks of the CTA traversal order (planes are visited block by
  * block, t inside a block; zblk divides Lz; 0 in dw_set_tile = automatic), and
  * sgrp, the number of CTAs that share one tile of tx sites: each holds
@@ -270,7 +273,11 @@ int dw_solve_eo(dw_lattice *lat, void *x, const void *eta, const double *mf, int
  * dw_tune times every valid tile for (op, nrhs) at the lattice precision on
  * lattice-owned scratch fields (CUDA events on `stream`, median of a few
  * launches), keeps the fastest for later calls and returns it in *spt, *tx,
- * *variant, *zblk, *sgrp (any may be NULL).  Requires a loaded gauge field;
+ * *variant, *zblk, *sgrp (any may be NULL).  For nrhs > 1 it also chooses the
+ * order of the launch grid, which these five numbers do not report: the RHS
+ * innermost (the CTAs of one tile for successive RHS share its links in L2; the
+ * order dw_set_tile selects) or outermost (one RHS's sweep after another, each
+ * with the L2 reuse window of a single RHS).  Requires a loaded gauge field;
  * synchronises; must not be called while `stream` is being captured into a
  * graph.
  */

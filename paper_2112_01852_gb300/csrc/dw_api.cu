@@ -177,6 +177,7 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.c = lat->c;
     for (int r = 0; r < n; ++r) p.mf[r] = mf_host ? mf_host[r0 + r] : 0.0;
     const TileConfig cfg = force ? *force : pick_tile(lat, prec, op, nrhs);
+    p.rhs_outer = cfg.rhs_outer;
     p.norm_partials =
         norm_partials ? norm_partials + (size_t)r0 * dslash_ctas_per_rhs(lat, cfg) : nullptr;
     int rc;
@@ -392,8 +393,8 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
   if (!tile_valid(lat, prec, op, t))
     return fail(DW_ERR_ARG,
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d sgrp=%d for Ls=%d Lz=%d (slices "
-                "per thread must divide Ls, tx a multiple of 32, variant 0..8 (6, 7: Lx = 32 and "
-                "Dhop only; 8: FP16 Dhop, Lx even, Ls a multiple of 4 up to 16, spt 1, tx 32, "
+                "per thread must divide Ls, tx a multiple of 32, variant 0..8 (6, 7: Lx <= 32, "
+                "Lx*Ly a multiple of 32, Dhop only; 8: FP16 Dhop, Lx even, Ls a multiple of 4 up to 16, spt 1, tx 32, "
                 "sgrp 1), zblk dividing Lz, sgrp dividing Ls/spt and 1 for D^+, CTA within "
                 "the kernel's limits)",
                 spt, tx, variant, zblk, sgrp, lat->Ls, lat->dims[2]);

@@ -167,6 +167,7 @@ struct DslashParams {
   int tiles_per_plane;  // set by the launcher: CTAs per (x, y) plane
   int zblk;             // set by the launcher: z-blocks of the traversal order
   int sgrp;             // set by the launcher: CTAs per site tile (slice groups)
+  int rhs_outer;        // RHS the slowest index of the grid (else the fastest)
   int t_begin;          // output sites: the time slices t_begin .. t_begin + t_count - 1
   int t_count;          // (0: all Lt; the inputs are read on the whole lattice)
   int *status;          // lattice-owned device word; set nonzero when a bounded wait gives up
@@ -188,15 +189,17 @@ struct TileConfig {
   int variant;  // hop-phase load scheme, 0 .. kNumVariants-1 (see dw.h)
   int zblk;     // z-blocks of the CTA traversal order (divides Lz)
   int sgrp;     // CTAs sharing one tile of sites, each with Ls / (spt sgrp) thread rows
+  int rhs_outer;  // 1: the RHS are the slowest index of the launch grid (chosen by the tuner)
 };
 constexpr int kNumVariants = 9;
 
-// Variants 6 and 7 stage rows in shared memory: they need Lx = 32 (a 32-site
-// block is one x row), tiles of whole rows that tile the (x, y) plane, the
-// hopping term alone (Dhop, Dhop^+) and no t halos.
+// Variants 6 and 7 stage 32-site blocks of the (x, y) plane in shared memory:
+// they need Lx <= 32 (an x or y neighbour at most one block away), planes of
+// whole blocks (Lx Ly a multiple of 32), tiles of whole blocks that tile the
+// plane, the hopping term alone (Dhop, Dhop^+) and no t halos.
 inline bool rows_variant_ok(int op, int Lx, int Ly, int tx) {
-  return (op == OP_DHOP || op == OP_DHOP_DAG) && Lx == 32 && tx % 32 == 0 && tx / 32 <= Ly &&
-         (Lx * Ly) % tx == 0;
+  return (op == OP_DHOP || op == OP_DHOP_DAG) && Lx <= 32 && (Lx * Ly) % 32 == 0 &&
+         tx % 32 == 0 && tx <= Lx * Ly && (Lx * Ly) % tx == 0;
 }
 // Dynamic shared memory of variants 6 and 7: the barrier, then R + 2 rows
 // (y0-1 .. y0+R, or the ring slots) of the CTA's nsl slices at precision

@@ -1071,7 +1071,9 @@ struct RegCap {
 // output site of parity p.parity with field index xf = x4 / 2 (x4 the full
 // lexicographic index; Lx even), its neighbours are read from the field of the
 // other parity at their x4 / 2, and the links stay full-lattice.
-template <class P, int OP, int SPT, int VAR, bool CB = false>
+// GLX (variants 6, 7): row staging for any Lx <= 32 (general in-plane
+// neighbour indices); without it the kernel is specialised to Lx = 32.
+template <class P, int OP, int SPT, int VAR, bool CB = false, bool GLX = false>
 __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   using C = typename P::C;
   using vec = typename P::vec;
@@ -1088,12 +1090,17 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   // spinor's last use as a t-neighbour follows its first use by 2 Lz/zblk
   // planes instead of 2 Lz: the L2 then holds the reuse window.
   const int tx = blockDim.x;
-  const int rhs = blockIdx.x % p.nrhs;
+  // RHS innermost (consecutive CTAs: the same tile for successive RHS, which
+  // share its links in L2) or outermost (p.rhs_outer: one RHS's sweep after
+  // another, each with the reuse window of a single RHS)
+  const int ctas_per_rhs = gridDim.x / p.nrhs;
+  const int rhs = p.rhs_outer ? blockIdx.x / ctas_per_rhs : blockIdx.x % p.nrhs;
+  const int cta_in_rhs = p.rhs_outer ? blockIdx.x % ctas_per_rhs : blockIdx.x / p.nrhs;
   const int Lxf = CB ? (p.L[0] >> 1) : p.L[0];  // field sites per x row
   const int plane_sites = Lxf * p.L[1];
   int x4, xf, in_plane, sg;  // full site, field index, index in the (x, y) plane
   {
-    int id = blockIdx.x / p.nrhs;
+    int id = cta_in_rhs;
     sg = id % p.sgrp;  // slice group: the CTAs of one tile are adjacent
     id /= p.sgrp;
     const int tile = id % p.tiles_per_plane;
@@ -1180,22 +1187,26 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   }
 
   if constexpr (VAR == 6 || VAR == 7) {
-    // Rows path.  A tile is R = tx/32 whole x rows of one (z, t) plane; rows
-    // y0-1 .. y0+R of the CTA's slices (one contiguous run per row in the
-    // blocked layout) are bulk-copied into shared memory by one thread while
-    // the t and z hops run from global memory; the y and x hops then read
-    // their neighbours there.  Same hop order as variant 5, so the same sums.
-    // Variant 6: one tile per CTA.  Variant 7: the CTA walks the Ly/R tiles of
-    // its plane in y, keeping the rows in a ring of R + 2 slots (row v in slot
-    // (v + 1) mod (R + 2)): each step copies only its R new rows, the two rows
-    // shared with the previous tile stay, and the next step's t+ rows are
-    // prefetched into L2.
+    // Rows path.  The (x, y) plane of a (z, t) slice is nblk = Lx Ly / 32 whole
+    // 32-site blocks ("rows": one x row when Lx = 32, two when Lx = 16, a row
+    // and a part when Lx = 24); a tile is R = tx/32 consecutive blocks y0 ..
+    // y0+R-1.  Blocks y0-1 .. y0+R of the CTA's slices (one contiguous run per
+    // block in the blocked layout) are bulk-copied into shared memory by one
+    // thread while the t and z hops run from global memory; the y and x hops
+    // then read their neighbours there (with Lx <= 32 an x or y neighbour is
+    // at most one block from its site, so the staged blocks hold them all).
+    // Same hop order as variant 5, so the same sums.  Variant 6: one tile per
+    // CTA.  Variant 7: the CTA walks the nblk/R tiles of its plane, keeping the
+    // blocks in a ring of R + 2 slots (block v in slot (v + 1) mod (R + 2)):
+    // each step copies only its R new blocks, the two shared with the previous
+    // tile stay, and the next step's t+ blocks are prefetched into L2.
     constexpr bool RING = (VAR == 7);
     constexpr int NPV = 24 / P::R;
     const int nsl = nchunk * SPT;  // slices of this CTA
     const int sbase = sg * nsl;
     const int R = tx / 32;
-    const int Ly = p.L[1];
+    const int Lx = p.L[0];
+    const int nblk = (Lx * p.L[1]) >> 5;  // 32-site blocks of a plane
     const int NR = R + 2;  // row slots
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw);
     vec *rows = reinterpret_cast<vec *>(smem_raw + 128);
@@ -1204,7 +1215,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     const int plane_base = x4 - in_plane;  // x4 of site 0 of the plane
     const int plane_blk = plane_base >> 5;  // block of row 0 of the plane
-    const int steps = RING ? (p.L[0] * Ly) / tx : 1;
+    const int steps = RING ? (Lx * p.L[1]) / tx : 1;
     const C zero = C(0);  // the hopping term alone: no (b + cK) combination
     const int sl = (int)threadIdx.y * SPT;  // = s0 - sbase
     if (leader) mbar_init(bar, 1);
@@ -1221,8 +1232,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         mbar_expect_tx(bar, row_bytes * (unsigned)n);
         for (int r = 0; r < n; ++r) {
-          const int v = first + r;  // virtual row, -1 .. Ly
-          const int y = v < 0 ? v + Ly : (v >= Ly ? v - Ly : v);
+          const int v = first + r;  // virtual block, -1 .. nblk
+          const int y = v < 0 ? v + nblk : (v >= nblk ? v - nblk : v);
           const int slot = RING ? (v + 1) % NR : r;
           const vec *src = F.base + ((long long)(plane_blk + y) * Ls + sbase) * NPV * 32;
           bulk_g2s(rows + (size_t)slot * row_vecs, src, row_bytes, bar);
@@ -1230,7 +1241,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         if (RING && k + 1 < steps) {
           // the t+ neighbours are the first touch of their plane (read from
           // HBM): fetch the next step's into L2 while this step runs
-          const int LyLz = Ly * p.L[2];
+          const int LyLz = nblk * p.L[2];  // blocks of a t slice
           const int tc = plane_blk / LyLz;
           const int tp_blk = plane_blk + (tc == p.L[3] - 1 ? -(p.L[3] - 1) : 1) * LyLz;
           for (int r = 0; r < R; ++r) {
@@ -1263,22 +1274,41 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       S.base = rows;
       S.V4 = 0;
       S.Ls = nsl;
-      const int ry = (ip >> 5) - y0;  // row of this site in the tile
-      const int xl = ip & 31;
-      // slots of the rows below, at and above this site's row
-      const int sdn = RING ? (y0 + ry) % NR : ry;
-      const int sat = RING ? (y0 + ry + 1) % NR : ry + 1;
-      const int sup = RING ? (y0 + ry + 2) % NR : ry + 2;
+      // staged index of the in-plane site q (virtual: q < 0 and q >= Lx Ly are
+      // the neighbouring rows across the periodic y edge, in blocks -1, nblk)
+      int iyp, iym, ixp, ixm;
+      if constexpr (!GLX) {  // Lx = 32: a block is one x row: the row's slot and the lane
+        const int ry = (ip >> 5) - y0;  // row of this site in the tile
+        const int xl = ip & 31;
+        const int sdn = RING ? (y0 + ry) % NR : ry;
+        const int sat = RING ? (y0 + ry + 1) % NR : ry + 1;
+        const int sup = RING ? (y0 + ry + 2) % NR : ry + 2;
+        iyp = sup * 32 + xl;
+        iym = sdn * 32 + xl;
+        ixp = sat * 32 + ((xl + 1) & 31);
+        ixm = sat * 32 + ((xl + 31) & 31);
+      } else {
+        auto sidx = [&](int q) {
+          const int v = (q + 32) / 32 - 1;  // floor(q / 32) for q >= -32
+          const int slot = RING ? (v + 1) % NR : v - (y0 - 1);
+          return slot * 32 + (q - 32 * v);
+        };
+        const int xc = ip % Lx;
+        iyp = sidx(ip + Lx);
+        iym = sidx(ip - Lx);
+        ixp = sidx(xc == Lx - 1 ? ip - (Lx - 1) : ip + 1);
+        ixm = sidx(xc == 0 ? ip + (Lx - 1) : ip - 1);
+      }
       hop_dir<P, 1, SF, false, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<1, true>(p), sup * 32 + xl, xs, sl, nsl, zero, zero, zero);
+          acc, S, gauge, (C)H.sign<1, true>(p), iyp, xs, sl, nsl, zero, zero, zero);
       hop_dir<P, 1, SB, true, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<1, false>(p), sdn * 32 + xl, H.nb<1, false>(p), sl, nsl, zero,
+          acc, S, gauge, (C)H.sign<1, false>(p), iym, H.nb<1, false>(p), sl, nsl, zero,
           zero, zero);
       hop_dir<P, 0, SF, false, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<0, true>(p), sat * 32 + ((xl + 1) & 31), xs, sl, nsl, zero,
+          acc, S, gauge, (C)H.sign<0, true>(p), ixp, xs, sl, nsl, zero,
           zero, zero);
       hop_dir<P, 0, SB, true, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<0, false>(p), sat * 32 + ((xl + 31) & 31), H.nb<0, false>(p),
+          acc, S, gauge, (C)H.sign<0, false>(p), ixm, H.nb<0, false>(p),
           sl, nsl, zero, zero, zero);
       if (RING) {
 #pragma unroll
@@ -1415,7 +1445,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (tid == 0)
-          p.norm_partials[(long long)rhs * (gridDim.x / p.nrhs) + blockIdx.x / p.nrhs] = v;
+          p.norm_partials[(long long)rhs * ctas_per_rhs + cta_in_rhs] = v;
       }
     }
   } else {
@@ -1483,23 +1513,24 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   }
 }
 
-template <class P, int OP, int SPT, int VAR, bool CB>
+template <class P, int OP, int SPT, int VAR, bool CB, bool GLX>
 __global__ void dslash_kernel(const DslashParams p) {
-  dslash_body<P, OP, SPT, VAR, CB>(p);
+  dslash_body<P, OP, SPT, VAR, CB, GLX>(p);
 }
 
-template <class P, int OP, int SPT, int VAR, bool CB>
+template <class P, int OP, int SPT, int VAR, bool CB, bool GLX>
 __global__ void __maxnreg__(RegCap<VAR>::value) dslash_kernel_capped(const DslashParams p) {
-  dslash_body<P, OP, SPT, VAR, CB>(p);
+  dslash_body<P, OP, SPT, VAR, CB, GLX>(p);
 }
 
-// The kernel entry of (P, OP, SPT, VAR, CB): variants 4, 6, 7 are register capped.
-template <class P, int OP, int SPT, int VAR, bool CB = false>
+// The kernel entry of (P, OP, SPT, VAR, CB, GLX): variants 4, 6, 7 are register
+// capped.
+template <class P, int OP, int SPT, int VAR, bool CB = false, bool GLX = false>
 constexpr void (*dslash_entry())(const DslashParams) {
   if constexpr (RegCap<VAR>::value > 0)
-    return dslash_kernel_capped<P, OP, SPT, VAR, CB>;
+    return dslash_kernel_capped<P, OP, SPT, VAR, CB, GLX>;
   else
-    return dslash_kernel<P, OP, SPT, VAR, CB>;
+    return dslash_kernel<P, OP, SPT, VAR, CB, GLX>;
 }
 
 template <class P, int OP, int SPT, int VAR>
@@ -1511,8 +1542,8 @@ size_t dslash_smem(int tx, int nchunk) {
   return smem;
 }
 
-template <class P, int OP, int SPT, int VAR, bool CB = false>
-int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t st) {
+template <class P, int OP, int SPT, int VAR, bool CB, bool GLX>
+int launch_one_k(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t st) {
   // D^+ exchanges slice-group edges through shared memory: one CTA per tile
   if (sgrp < 1 || (p.Ls / SPT) % sgrp || (OP == OP_DDAG && sgrp != 1)) return -2;
   // checkerboard launches: register variants only, Lx even, no halos
@@ -1542,21 +1573,30 @@ int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t s
   static size_t smem_set = 48 * 1024;
   if (!max_threads) {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dslash_entry<P, OP, SPT, VAR, CB>()) != cudaSuccess)
+    if (cudaFuncGetAttributes(&fa, dslash_entry<P, OP, SPT, VAR, CB, GLX>()) != cudaSuccess)
       return -1;
     max_threads = fa.maxThreadsPerBlock;
   }
   if (tx < 32 || tx % 32 || tx * nchunk > max_threads) return -3;
   if (smem > 227 * 1024) return -3;
   if (smem > smem_set) {
-    if (cudaFuncSetAttribute(dslash_entry<P, OP, SPT, VAR, CB>(),
+    if (cudaFuncSetAttribute(dslash_entry<P, OP, SPT, VAR, CB, GLX>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return -3;
     smem_set = smem;
   }
-  dslash_entry<P, OP, SPT, VAR, CB>()<<<grid, block, smem, st>>>(q);
+  dslash_entry<P, OP, SPT, VAR, CB, GLX>()<<<grid, block, smem, st>>>(q);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Variants 6 and 7 take their general-Lx form unless Lx = 32.
+template <class P, int OP, int SPT, int VAR, bool CB = false>
+int launch_one(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t st) {
+  if constexpr (VAR == 6 || VAR == 7) {
+    if (p.L[0] != 32) return launch_one_k<P, OP, SPT, VAR, CB, true>(p, tx, zblk, sgrp, st);
+  }
+  return launch_one_k<P, OP, SPT, VAR, CB, false>(p, tx, zblk, sgrp, st);
 }
 
 template <class P, int OP, int VAR, bool CB = false>

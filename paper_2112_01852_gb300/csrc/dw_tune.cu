@@ -35,8 +35,9 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
     for (int spt : {1, 2, 3, 4})
       for (int tx : {32, 64, 128, 256})
         for (int zblk : zbs)
-          for (int sgrp : {1, 2, 3, 4, 6}) {
-            TileConfig t{spt, tx, variant, zblk, sgrp};
+          for (int sgrp : {1, 2, 3, 4, 6})
+          for (int outer = 0; outer < (nrhs > 1 ? 2 : 1); ++outer) {
+            TileConfig t{spt, tx, variant, zblk, sgrp, outer};
             if (quick && tx > 128) continue;
             if (!tile_valid(lat, prec, op, t)) continue;
             // warm-up launch doubles as the validity check

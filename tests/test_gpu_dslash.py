@@ -131,14 +131,16 @@ def test_slice_groups_equal_one_cta(prec):
 
 
 @pytest.mark.parametrize("prec", [dw.DW_F32, dw.DW_F16], ids=["f32", "f16"])
-@pytest.mark.parametrize("dims", [(32, 4, 2, 6), (32, 2, 2, 4), (32, 1, 2, 4)],
-                         ids=["Ly4", "Ly2", "Ly1"])
+@pytest.mark.parametrize("dims", [(32, 4, 2, 6), (32, 2, 2, 4), (32, 1, 2, 4), (16, 4, 2, 4),
+                                  (24, 4, 2, 4), (8, 8, 2, 4), (16, 2, 2, 4)],
+                         ids=["Ly4", "Ly2", "Ly1", "Lx16", "Lx24", "Lx8", "one_block"])
 def test_row_staged_variant(prec, dims):
-    # variants 6 and 7 read the x and y neighbours from rows staged in shared
-    # memory (7 walking the plane's tiles with a ring of rows); they sum the
-    # same terms in the same order as variant 5: equal bit for bit, and within
-    # tolerance of the oracle.  Ly = 2 and 1: the halo rows repeat rows of the
-    # tile (and the ring wraps within one step).
+    # variants 6 and 7 read the x and y neighbours from 32-site blocks of the
+    # plane staged in shared memory (7 walking the plane's tiles with a ring of
+    # blocks); they sum the same terms in the same order as variant 5: equal
+    # bit for bit, and within tolerance of the oracle.  Ly = 2 and 1 at Lx = 32,
+    # and a plane of one block: the halo blocks repeat blocks of the tile (and
+    # the ring wraps within one step); Lx = 24: a block holds a row and a part.
     Ls = 4
     U, psi = make_case(dims, Ls, 2, seed=17)
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
@@ -167,8 +169,11 @@ def test_row_staged_variant(prec, dims):
     lat.close()
 
 
-def test_row_staged_variant_needs_lx32():
-    dims, Ls = (16, 4, 2, 4), 4
+@pytest.mark.parametrize("dims", [(48, 2, 2, 4), (12, 4, 2, 4)], ids=["Lx48", "plane48"])
+def test_row_staged_variant_limits(dims):
+    # Lx > 32 (a y neighbour two blocks away) or a plane that is not a whole
+    # number of 32-site blocks: the row-staged variants refuse the tile
+    Ls = 4
     U, _ = make_case(dims, Ls, 1, seed=18)
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
     lat.load_gauge(U)
