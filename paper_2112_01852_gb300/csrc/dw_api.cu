@@ -142,8 +142,11 @@ long long dslash_ctas_per_rhs(const dw_lattice *lat, TileConfig t) {
 int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
                const int *gate, int gate_stride, const void *halo_up, const void *halo_dn,
-               double *norm_partials, int t_begin, int t_count) {
+               double *norm_partials, int t_begin, int t_count, const ResidualFuse *fuse) {
   const size_t rhs_bytes = field_bytes(lat, prec, 1);
+  const int rs_prec = prec == DW_F64 ? DW_F64 : DW_F32;  // the residual's precision
+  const size_t rs_rhs_bytes = field_bytes(lat, rs_prec, 1);
+  if (fuse && op != OP_DDAG) return fail(DW_ERR_ARG, "the fused residual update is D^+ only");
   const size_t hrhs_bytes = halo_bytes(lat, prec, 1);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
     const int n = (nrhs - r0) < kMaxRhsPerLaunch ? (nrhs - r0) : kMaxRhsPerLaunch;
@@ -180,6 +183,13 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
     p.rhs_outer = cfg.rhs_outer;
     p.norm_partials =
         norm_partials ? norm_partials + (size_t)r0 * dslash_ctas_per_rhs(lat, cfg) : nullptr;
+    if (fuse) {
+      p.rs = (char *)fuse->r_s + (size_t)r0 * rs_rhs_bytes;
+      p.rs_stride = lat->V4p * lat->Ls * (24 / prec_reals_per_vec(rs_prec));
+      p.rs_alpha = fuse->alpha + (size_t)r0 * fuse->alpha_stride;
+      p.rs_alpha_stride = fuse->alpha_stride;
+      p.rs_partials = fuse->partials + (size_t)r0 * dslash_ctas_per_rhs(lat, cfg);
+    }
     int rc;
     if (lat->cplx && prec == DW_F32) {
       if (op != OP_DHOP && op != OP_DHOP_DAG)
@@ -197,7 +207,12 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
       return fail(DW_ERR_ARG,
                   "tile (spt=%d, tx=%d, variant=%d) exceeds the kernel's CTA limits", cfg.spt,
                   cfg.tx, cfg.variant);
-    if (rc) return cuda_fail(cudaGetLastError(), "dslash launch");
+    if (rc) {
+      const cudaError_t e0 = cudaGetLastError();
+      const cudaError_t e = e0 != cudaSuccess ? e0 : last_launch_error();
+      return fail(DW_ERR_CUDA, "dslash launch (op %d, precision %d, tile %d,%d,%d,%d,%d): %s", op,
+                  prec, cfg.spt, cfg.tx, cfg.variant, cfg.zblk, cfg.sgrp, cudaGetErrorString(e));
+    }
   }
   return DW_OK;
 }

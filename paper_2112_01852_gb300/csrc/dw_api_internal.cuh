@@ -27,11 +27,13 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
 // only) receives |out|^2 per CTA, [rhs][dslash_ctas_per_rhs]; t_begin / t_count
 // restrict the output to the time slices t_begin .. t_begin + t_count - 1
 // (t_count 0: all).
+// `fuse` (optional, OP_DDAG only): the CG residual update of ResidualFuse in place
+// of storing out (out is then not written).
 int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
                const double *mf_host, int nrhs, cudaStream_t st, const TileConfig *force,
                const int *gate = nullptr, int gate_stride = 0, const void *halo_up = nullptr,
                const void *halo_dn = nullptr, double *norm_partials = nullptr, int t_begin = 0,
-               int t_count = 0);
+               int t_count = 0, const ResidualFuse *fuse = nullptr);
 // CTAs per right-hand side of a stencil launch with tile `t` (the length of the
 // per-RHS rows of norm_partials).
 long long dslash_ctas_per_rhs(const dw_lattice *lat, TileConfig t);

@@ -554,8 +554,9 @@ int cg_alpha(const BlasCtx &c, const double *partial, int nblk, CGState *st, cud
 }
 
 int cg_beta(const BlasCtx &c, const double *partial, CGState *st, double delta, double tol,
-            int maxit, cudaStream_t s) {
-  cg_beta_kernel<<<c.nrhs, kSumThreads, 0, s>>>(partial, c.nblk, st, delta, tol, maxit);
+            int maxit, cudaStream_t s, int nblk) {
+  cg_beta_kernel<<<c.nrhs, kSumThreads, 0, s>>>(partial, nblk < 0 ? c.nblk : nblk, st, delta,
+                                                tol, maxit);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

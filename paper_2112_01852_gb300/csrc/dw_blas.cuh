@@ -73,8 +73,10 @@ int cg_direction(const BlasCtx &c, int pp, int pr, void *p, void *x_s, const voi
                  const CGState *st, cudaStream_t s);
 // alpha = rr / <p, Ap> with <p, Ap> summed from nblk partials per RHS.
 int cg_alpha(const BlasCtx &c, const double *partial, int nblk, CGState *st, cudaStream_t s);
+// nblk: partials per RHS (-1: c.nblk, the BLAS grid; a fused D^+ pass leaves one
+// per stencil CTA)
 int cg_beta(const BlasCtx &c, const double *partial, CGState *st, double delta, double tol,
-            int maxit, cudaStream_t s);
+            int maxit, cudaStream_t s, int nblk = -1);
 int cg_reliable(const BlasCtx &c, const double *partial, CGState *st, double tol, int maxit,
                 int first, cudaStream_t s);
 int cg_install(const BlasCtx &c, CGState *st, cudaStream_t s);

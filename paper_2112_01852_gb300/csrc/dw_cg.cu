@@ -20,6 +20,7 @@
 // host checks of the flags.
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -41,6 +42,8 @@ struct CGWork {
   size_t sums_cap = 0;
   double *dnorm = nullptr;  // |D p|^2 per stencil CTA
   size_t dnorm_cap = 0;
+  double *rsnorm = nullptr;  // |r_s|^2 per CTA of the fused D^+ pass
+  size_t rsnorm_cap = 0;
   CGState *state = nullptr;
   size_t state_cap = 0;
   // even-odd solves: even-parity intermediates of Dhat (inner precision and
@@ -56,7 +59,7 @@ void cg_release(dw_lattice *lat) {
   CGWork *w = lat->cg;
   if (!w) return;
   void *bufs[] = {w->r64,  w->Ax64,  w->tmp64, w->p,     w->Ap,   w->tmp,   w->rs,
-                  w->xs,   w->partials, w->sums, w->dnorm, w->state, w->e1,    w->e2,
+                  w->xs,   w->partials, w->sums, w->dnorm, w->rsnorm, w->state, w->e1, w->e2,
                   w->e1_64, w->e2_64, w->eta_e, w->eta_o, w->bhat, w->bpr,  w->xo};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -90,7 +93,14 @@ struct Solve {
     return (int)(eo ? cb_ctas_per_rhs(lat, pp, OP_D)
                     : dslash_ctas_per_rhs(lat, pick_tile(lat, pp, OP_D, nrhs)));
   }
+  int ctas_ddag() const {
+    return (int)dslash_ctas_per_rhs(lat, pick_tile(lat, pp, OP_DDAG, nrhs));
+  }
 
+  // Unpreconditioned: alpha follows from the D pass (|D p|^2), so the D^+ pass
+  // applies r_s -= alpha D^+D p itself and leaves |r_s|^2 per CTA: D^+D p is
+  // never stored and read back (two field passes fewer than D^+ followed by
+  // cg_update).
   int iteration() {
     const int nd = ctas_d();
     int rc;
@@ -100,18 +110,26 @@ struct Solve {
       if (rc) return rc;
       rc = apply_schur(lat, pp, w->Ap, w->tmp, mf, nrhs, true, w->e1, w->e2, st, gate_run(),
                        kCGStateInts, nullptr);
+      if (rc) return rc;
+      if (cg_alpha(c, w->dnorm, nd, w->state, st) ||
+          cg_update(c, pp, pr, w->rs, w->Ap, w->partials, w->state, st) ||
+          cg_beta(c, w->partials, w->state, delta, tol, maxit, st))
+        return cuda_fail(cudaGetLastError(), "cg iteration launch");
     } else {
       rc = run_dslash(lat, pp, OP_D, w->tmp, w->p, mf, nrhs, st, nullptr, gate_run(),
                       kCGStateInts, nullptr, nullptr, w->dnorm);
       if (rc) return rc;
+      if (cg_alpha(c, w->dnorm, nd, w->state, st))
+        return cuda_fail(cudaGetLastError(), "cg iteration launch");
+      const ResidualFuse fuse{w->rs, &w->state[0].alpha,
+                              (int)(sizeof(CGState) / sizeof(double)), w->rsnorm};
       rc = run_dslash(lat, pp, OP_DDAG, w->Ap, w->tmp, mf, nrhs, st, nullptr, gate_run(),
-                      kCGStateInts);
+                      kCGStateInts, nullptr, nullptr, nullptr, 0, 0, &fuse);
+      if (rc) return rc;
+      if (cg_beta(c, w->rsnorm, w->state, delta, tol, maxit, st, ctas_ddag()))
+        return cuda_fail(cudaGetLastError(), "cg iteration launch");
     }
-    if (rc) return rc;
-    if (cg_alpha(c, w->dnorm, nd, w->state, st) ||
-        cg_update(c, pp, pr, w->rs, w->Ap, w->partials, w->state, st) ||
-        cg_beta(c, w->partials, w->state, delta, tol, maxit, st) ||
-        cg_direction(c, pp, pr, w->p, w->xs, w->rs, w->state, st))
+    if (cg_direction(c, pp, pr, w->p, w->xs, w->rs, w->state, st))
       return cuda_fail(cudaGetLastError(), "cg iteration launch");
     return DW_OK;
   }
@@ -147,6 +165,10 @@ struct Solve {
 };
 
 int ensure(void **buf, size_t *cap, size_t need) { return ensure_buffer(buf, cap, need); }
+
+// the fused D^+ pass reads alpha of RHS r at (double *)&state[0].alpha + r * stride
+static_assert(sizeof(CGState) % sizeof(double) == 0 && offsetof(CGState, alpha) % sizeof(double) == 0,
+              "CGState must be a whole number of doubles with alpha double-aligned");
 
 }  // namespace
 
@@ -237,6 +259,9 @@ int cg_run(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs, 
   {
     const long long nd = S.ctas_d();
     if ((rc = ensure((void **)&w->dnorm, &w->dnorm_cap, sizeof(double) * (size_t)nd * nrhs)))
+      return rc;
+    if (!eo && (rc = ensure((void **)&w->rsnorm, &w->rsnorm_cap,
+                            sizeof(double) * (size_t)S.ctas_ddag() * nrhs)))
       return rc;
   }
 

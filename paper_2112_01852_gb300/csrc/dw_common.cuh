@@ -178,6 +178,22 @@ struct DslashParams {
   double hscale;        // factor of the hopping term (-1/2 in D_W)
   double M5, b, c;
   double mf[64];         // per-RHS masses, passed by value
+  // optional (OP_DDAG, the CG's D^+ pass): instead of storing out, update the
+  // CG residual r_s -= alpha_rhs out in place (r_s at FP64 for FP64 operators,
+  // FP32 otherwise) and leave |r_s|^2 per CTA in rs_partials [rhs][CTA]
+  void *rs;
+  long long rs_stride;    // vecs of r_s per RHS
+  const double *rs_alpha;  // alpha of RHS r at rs_alpha[r * rs_alpha_stride]
+  int rs_alpha_stride;
+  double *rs_partials;
+};
+
+// The residual update fused into a D^+ launch (see DslashParams::rs).
+struct ResidualFuse {
+  void *r_s;
+  const double *alpha;
+  int alpha_stride;
+  double *partials;
 };
 
 constexpr int kMaxRhsPerLaunch = 64;
@@ -207,6 +223,10 @@ inline bool rows_variant_ok(int op, int Lx, int Ly, int tx) {
 inline size_t rows_smem_bytes(int tx, int nsl, int prec) {
   return 128 + (size_t)(tx / 32 + 2) * nsl * 24 * 32 * prec_real_bytes(prec);
 }
+
+// The error of the last stencil launch that failed on this thread (the launch
+// itself clears CUDA's last-error state when it checks it).
+cudaError_t &last_launch_error();
 
 // Stencil launch at precision `prec`: 0 on success, -2 for a tile/variant
 // that does not exist, -3 for a CTA beyond the kernel's limits, -1 on a CUDA

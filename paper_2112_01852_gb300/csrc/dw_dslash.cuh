@@ -1465,6 +1465,12 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       }
     }
     __syncthreads();
+    // fused CG residual update (p.rs): r_s at FP64 for FP64 operators, else FP32
+    using PR = typename std::conditional<std::is_same<C, double>::value, F64, F32>::type;
+    using rvec = typename PR::vec;
+    constexpr int RNPV = 24 / PR::R;
+    constexpr int RVPQ = 4 / PR::R;
+    double rsq = 0.0;
     if (active) {
       const int cn = (chunk + 1 == nchunk) ? 0 : chunk + 1;
       const int cp = (chunk == 0) ? nchunk - 1 : chunk - 1;
@@ -1496,7 +1502,29 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
           o.lo.re[cc] = p_fma(mc, klr, p_fma(mb, acc[j].lo.re[cc], v.lo.re[cc]));
           o.lo.im[cc] = p_fma(mc, kli, p_fma(mb, acc[j].lo.im[cc], v.lo.im[cc]));
         }
-        store(j, o);
+        if (p.rs) {
+          const V2 na = bc<V2>(-(C)p.rs_alpha[(long long)rhs * p.rs_alpha_stride]);
+          rvec *rb = reinterpret_cast<rvec *>(p.rs) + (long long)rhs * p.rs_stride +
+                     site_off(xf, s0 + j, Ls, RNPV);
+          C ss = 0;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const Half<V2> &oh = h ? o.lo : o.up;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+              rvec *q = rb + (long long)(h * 3 + cc) * RVPQ * kPlaneStride;
+              V2 rr, ri;
+              quad_in(rr, ri, q, kPlaneStride);
+              rr = p_fma(na, oh.re[cc], rr);
+              ri = p_fma(na, oh.im[cc], ri);
+              ss += rr.x * rr.x + rr.y * rr.y + ri.x * ri.x + ri.y * ri.y;
+              quad_out(q, kPlaneStride, rr, ri);
+            }
+          }
+          rsq += (double)ss;
+        } else {
+          store(j, o);
+        }
       };
       if (p.own) {
         roll_5d<P, true, SPT>(Fo, xf, s0, Ls, alpha, beta, mf, emit);
@@ -1508,6 +1536,22 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         }
 #pragma unroll
         for (int j = 0; j < SPT; ++j) emit(j, zero_v);
+      }
+    }
+    if (p.rs) {
+      // fixed-order block sum of |r_s|^2, as for the norm of the D pass
+      __shared__ double rs_warp[32];
+      const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+      const int nwarps = (blockDim.x * blockDim.y + 31) / 32;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rsq += __shfl_down_sync(0xffffffffu, rsq, o);
+      if ((tid & 31) == 0) rs_warp[tid >> 5] = rsq;
+      __syncthreads();
+      if (tid < 32) {
+        double v = tid < nwarps ? rs_warp[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (tid == 0) p.rs_partials[(long long)rhs * ctas_per_rhs + cta_in_rhs] = v;
       }
     }
   }
@@ -1568,17 +1612,25 @@ int launch_one_k(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t
   if (q.t_begin < 0 || q.t_count < 1 || q.t_begin + q.t_count > p.L[3]) return -2;
   dim3 grid((unsigned)((long long)q.tiles_per_plane * sgrp * p.L[2] * q.t_count * p.nrhs));
   const size_t smem = dslash_smem<P, OP, SPT, VAR>(tx, nchunk);
-  // per-instantiation launch limits, queried once
+  // per-instantiation launch limits, queried once; the dynamic shared memory
+  // a launch may use without raising the kernel's limit is 48 KB less the
+  // kernel's static shared memory
   static int max_threads = 0;
-  static size_t smem_set = 48 * 1024;
+  static size_t static_smem = 0;
+  static size_t smem_set = 0;
   if (!max_threads) {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dslash_entry<P, OP, SPT, VAR, CB, GLX>()) != cudaSuccess)
+    const cudaError_t e = cudaFuncGetAttributes(&fa, dslash_entry<P, OP, SPT, VAR, CB, GLX>());
+    if (e != cudaSuccess) {
+      last_launch_error() = e;
       return -1;
+    }
+    static_smem = fa.sharedSizeBytes;
+    smem_set = 48 * 1024 > static_smem ? 48 * 1024 - static_smem : 0;
     max_threads = fa.maxThreadsPerBlock;
   }
   if (tx < 32 || tx % 32 || tx * nchunk > max_threads) return -3;
-  if (smem > 227 * 1024) return -3;
+  if (smem + static_smem > 227 * 1024) return -3;
   if (smem > smem_set) {
     if (cudaFuncSetAttribute(dslash_entry<P, OP, SPT, VAR, CB, GLX>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -1587,7 +1639,10 @@ int launch_one_k(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t
     smem_set = smem;
   }
   dslash_entry<P, OP, SPT, VAR, CB, GLX>()<<<grid, block, smem, st>>>(q);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return 0;
+  last_launch_error() = e;
+  return -1;
 }
 
 // Variants 6 and 7 take their general-Lx form unless Lx = 32.

@@ -5,6 +5,11 @@
 
 namespace dw {
 
+cudaError_t &last_launch_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
 int launch_dslash_F64_v0(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
 int dslash_max_threads_F64_v0(int op, int spt);
 int launch_dslash_F64_v2(const DslashParams &p, int op, TileConfig cfg, cudaStream_t st);
