@@ -65,13 +65,14 @@ int apply_m5(dw_lattice *lat, int prec, void *out, const void *in, const double 
 int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr, const void *own,
                   int parity, double alpha, double beta, double hscale, const double *mf,
                   int nrhs, cudaStream_t st, const int *gate, int gate_stride,
-                  double *norm_partials, const TileConfig *force = nullptr);
+                  double *norm_partials, const TileConfig *force = nullptr,
+                  const ResidualFuse *fuse = nullptr);
 long long cb_ctas_per_rhs(const dw_lattice *lat, int prec, int op);
 // Time the checkerboard tiles of (prec, op) once per lattice and keep the best.
 int tune_cb(dw_lattice *lat, int prec, int op, cudaStream_t st);
 // out_o = Dhat in_o or Dhat^+ in_o; t1, t2 even scratch fields
 int apply_schur(dw_lattice *lat, int prec, void *out, const void *in, const double *mf, int nrhs,
                 bool dag, void *t1, void *t2, cudaStream_t st, const int *gate, int gate_stride,
-                double *norm_partials);
+                double *norm_partials, const ResidualFuse *fuse = nullptr);
 
 }  // namespace dw

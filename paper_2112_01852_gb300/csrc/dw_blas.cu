@@ -229,42 +229,6 @@ __global__ void __launch_bounds__(kBlasThreads)
   }
 }
 
-// CG step: r_s -= alpha Ap;  partial |r_s|^2  (active RHS only).  The
-// x_s += alpha p of the same step is done by cg_direction_kernel.
-template <class PP, class PR>
-__global__ void __launch_bounds__(kBlasThreads)
-    cg_update_kernel(void *r_s, const void *Ap, SlotGeom L, size_t bpp, size_t bpr,
-                     double *partial, const CGState *st) {
-  const int rhs = blockIdx.y;
-  const CGState &S = st[rhs];
-  double s = 0.0;
-  if (S.run) {
-    const double alpha = S.alpha;
-    void *prs = RHS_PTR(char *, r_s, rhs, bpr);
-    const void *pap = RHS_PTR(const char *, Ap, rhs, bpp);
-    using A = typename Arith<PP, PR>::T;
-    const A a = (A)alpha;
-    SLOT_LOOP(i) {
-      A site = 0;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        A rv[4], av[4];
-        ld4<PR>(rv, prs, q, i);
-        ld4<PP>(av, pap, q, i);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          rv[k] -= a * av[k];
-          site += rv[k] * rv[k];
-        }
-        st4<PR>(prs, q, i, rv);
-      }
-      s += (double)site;
-    }
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) partial[(size_t)rhs * gridDim.x + blockIdx.x] = s;
-}
-
 // x_s += alpha p for every RHS whose step computed alpha (including those that
 // now wait for a reliable update), then p = r_s + beta p for those that go on
 // iterating: one read of p serves both.
@@ -527,15 +491,6 @@ int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r
       reliable_apply_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
           r, r_s, x_s, p, c.geom, rbytes(DW_F64, c.geom), rbytes(pp, c.geom), rbytes(pr, c.geom),
           st)));
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-int cg_update(const BlasCtx &c, int pp, int pr, void *r_s, const void *Ap, double *partial,
-              const CGState *st, cudaStream_t s) {
-  dim3 grid(c.nblk, c.nrhs);
-  DISPATCH_PREC(pp, PP, DISPATCH_PREC(pr, PR,
-      cg_update_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
-          r_s, Ap, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), partial, st)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -64,11 +64,8 @@ int cg_accumulate_x(const BlasCtx &c, int pr, void *x, const void *x_s, const CG
                     cudaStream_t s);
 int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r_s, void *x_s,
                       void *p, const CGState *st, cudaStream_t s);
-// r_s -= alpha Ap with |r_s|^2 partials; the x_s update waits for cg_direction,
-// which reads p once for x_s += alpha p and p = r_s + beta p (8 field passes
-// per iteration instead of 9).
-int cg_update(const BlasCtx &c, int pp, int pr, void *r_s, const void *Ap, double *partial,
-              const CGState *st, cudaStream_t s);
+// x_s += alpha p and p = r_s + beta p with one read of p (the r_s -= alpha Ap
+// of the step is fused into the D^+ pass, see DslashParams::rs).
 int cg_direction(const BlasCtx &c, int pp, int pr, void *p, void *x_s, const void *r_s,
                  const CGState *st, cudaStream_t s);
 // alpha = rr / <p, Ap> with <p, Ap> summed from nblk partials per RHS.

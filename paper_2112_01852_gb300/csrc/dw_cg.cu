@@ -94,41 +94,37 @@ struct Solve {
                     : dslash_ctas_per_rhs(lat, pick_tile(lat, pp, OP_D, nrhs)));
   }
   int ctas_ddag() const {
-    return (int)dslash_ctas_per_rhs(lat, pick_tile(lat, pp, OP_DDAG, nrhs));
+    return (int)(eo ? cb_ctas_per_rhs(lat, pp, OP_DDAG)
+                    : dslash_ctas_per_rhs(lat, pick_tile(lat, pp, OP_DDAG, nrhs)));
   }
 
-  // Unpreconditioned: alpha follows from the D pass (|D p|^2), so the D^+ pass
-  // applies r_s -= alpha D^+D p itself and leaves |r_s|^2 per CTA: D^+D p is
-  // never stored and read back (two field passes fewer than D^+ followed by
-  // cg_update).
+  // alpha follows from the D (Dhat) pass, |D p|^2, so the last launch of the
+  // D^+ (Dhat^+) pass applies r_s -= alpha A p itself and leaves |r_s|^2 per CTA:
+  // A p is never stored and read back (two field passes fewer than storing it
+  // and updating r_s in a separate pass).
   int iteration() {
     const int nd = ctas_d();
     int rc;
-    if (eo) {
+    if (eo)
       rc = apply_schur(lat, pp, w->tmp, w->p, mf, nrhs, false, w->e1, w->e2, st, gate_run(),
                        kCGStateInts, w->dnorm);
-      if (rc) return rc;
-      rc = apply_schur(lat, pp, w->Ap, w->tmp, mf, nrhs, true, w->e1, w->e2, st, gate_run(),
-                       kCGStateInts, nullptr);
-      if (rc) return rc;
-      if (cg_alpha(c, w->dnorm, nd, w->state, st) ||
-          cg_update(c, pp, pr, w->rs, w->Ap, w->partials, w->state, st) ||
-          cg_beta(c, w->partials, w->state, delta, tol, maxit, st))
-        return cuda_fail(cudaGetLastError(), "cg iteration launch");
-    } else {
+    else
       rc = run_dslash(lat, pp, OP_D, w->tmp, w->p, mf, nrhs, st, nullptr, gate_run(),
                       kCGStateInts, nullptr, nullptr, w->dnorm);
-      if (rc) return rc;
-      if (cg_alpha(c, w->dnorm, nd, w->state, st))
-        return cuda_fail(cudaGetLastError(), "cg iteration launch");
-      const ResidualFuse fuse{w->rs, &w->state[0].alpha,
-                              (int)(sizeof(CGState) / sizeof(double)), w->rsnorm};
+    if (rc) return rc;
+    if (cg_alpha(c, w->dnorm, nd, w->state, st))
+      return cuda_fail(cudaGetLastError(), "cg iteration launch");
+    const ResidualFuse fuse{w->rs, &w->state[0].alpha, (int)(sizeof(CGState) / sizeof(double)),
+                            w->rsnorm};
+    if (eo)
+      rc = apply_schur(lat, pp, w->Ap, w->tmp, mf, nrhs, true, w->e1, w->e2, st, gate_run(),
+                       kCGStateInts, nullptr, &fuse);
+    else
       rc = run_dslash(lat, pp, OP_DDAG, w->Ap, w->tmp, mf, nrhs, st, nullptr, gate_run(),
                       kCGStateInts, nullptr, nullptr, nullptr, 0, 0, &fuse);
-      if (rc) return rc;
-      if (cg_beta(c, w->rsnorm, w->state, delta, tol, maxit, st, ctas_ddag()))
-        return cuda_fail(cudaGetLastError(), "cg iteration launch");
-    }
+    if (rc) return rc;
+    if (cg_beta(c, w->rsnorm, w->state, delta, tol, maxit, st, ctas_ddag()))
+      return cuda_fail(cudaGetLastError(), "cg iteration launch");
     if (cg_direction(c, pp, pr, w->p, w->xs, w->rs, w->state, st))
       return cuda_fail(cudaGetLastError(), "cg iteration launch");
     return DW_OK;
@@ -260,8 +256,8 @@ int cg_run(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs, 
     const long long nd = S.ctas_d();
     if ((rc = ensure((void **)&w->dnorm, &w->dnorm_cap, sizeof(double) * (size_t)nd * nrhs)))
       return rc;
-    if (!eo && (rc = ensure((void **)&w->rsnorm, &w->rsnorm_cap,
-                            sizeof(double) * (size_t)S.ctas_ddag() * nrhs)))
+    if ((rc = ensure((void **)&w->rsnorm, &w->rsnorm_cap,
+                     sizeof(double) * (size_t)S.ctas_ddag() * nrhs)))
       return rc;
   }
 

@@ -293,8 +293,11 @@ long long cb_ctas_per_rhs(const dw_lattice *lat, int prec, int op) {
 int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr, const void *own,
                   int parity, double alpha, double beta, double hscale, const double *mf,
                   int nrhs, cudaStream_t st, const int *gate, int gate_stride,
-                  double *norm_partials, const TileConfig *force) {
+                  double *norm_partials, const TileConfig *force, const ResidualFuse *fuse) {
   const size_t rhs_bytes = cb_field_bytes(lat, prec, 1);
+  const int rs_prec = prec == DW_F64 ? DW_F64 : DW_F32;  // the residual's precision
+  const size_t rs_rhs_bytes = cb_field_bytes(lat, rs_prec, 1);
+  if (fuse && op != OP_DDAG) return fail(DW_ERR_ARG, "the fused residual update is D^+ only");
   const TileConfig cfg = force ? *force : cb_tile(lat, prec, op);
   const long long ctas = cb_ctas_per_rhs(lat, prec, op);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPerLaunch) {
@@ -325,6 +328,13 @@ int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr,
     p.c = lat->c;
     for (int r = 0; r < n; ++r) p.mf[r] = mf[r0 + r];
     p.norm_partials = norm_partials ? norm_partials + (size_t)r0 * ctas : nullptr;
+    if (fuse) {
+      p.rs = (char *)fuse->r_s + (size_t)r0 * rs_rhs_bytes;
+      p.rs_stride = padded_v4(lat->V4 / 2) * lat->Ls * (24 / prec_reals_per_vec(rs_prec));
+      p.rs_alpha = fuse->alpha + (size_t)r0 * fuse->alpha_stride;
+      p.rs_alpha_stride = fuse->alpha_stride;
+      p.rs_partials = fuse->partials + (size_t)r0 * ctas;
+    }
     const int rc = launch_dslash_cb(p, prec, op, cfg, st);
     if (rc == -2 || rc == -3)
       return fail(DW_ERR_ARG, "checkerboard stencil unavailable for this lattice");
@@ -334,10 +344,11 @@ int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr,
 }
 
 // out_o = Dhat in_o (dag: Dhat^+ in_o) at precision prec; t1, t2: even-parity
-// scratch fields; norm_partials (optional, not dag) receives |out|^2 per CTA.
+// scratch fields; norm_partials (optional, not dag) receives |out|^2 per CTA;
+// fuse (optional, dag only): the CG residual update in place of storing out.
 int apply_schur(dw_lattice *lat, int prec, void *out, const void *in, const double *mf, int nrhs,
                 bool dag, void *t1, void *t2, cudaStream_t st, const int *gate, int gate_stride,
-                double *norm_partials) {
+                double *norm_partials, const ResidualFuse *fuse) {
   const int op = dag ? OP_DDAG : OP_D;
   const double alpha = lat->b * (4.0 - lat->M5) + 1.0;
   const double beta = lat->c * (4.0 - lat->M5) - 1.0;
@@ -349,7 +360,8 @@ int apply_schur(dw_lattice *lat, int prec, void *out, const void *in, const doub
   if ((rc = apply_m5(lat, prec, t2, t1, mf, nrhs, true, dag, st))) return rc;
   // out = A in - H_oe t2  (A^+ in - H_eo^+ t2), on odd sites
   return run_dslash_cb(lat, prec, op, out, t2, in, 1, alpha, beta, 0.5, mf, nrhs, st, gate,
-                       gate_stride, dag ? nullptr : norm_partials);
+                       gate_stride, dag ? nullptr : norm_partials, nullptr,
+                       dag ? fuse : nullptr);
 }
 
 // Times the checkerboard tiles of (prec, op) on two scratch parity fields (the
