@@ -531,6 +531,9 @@ def main():
                     help="storage of the timed Dhop with --main-only (profiling runs)")
     ap.add_argument("--nrhs", type=int, default=1,
                     help="right-hand sides of the timed Dhop with --main-only (profiling runs)")
+    ap.add_argument("--op", default="dhop", choices=["dhop", "d", "ddag"],
+                    help="operator timed with --main-only (profiling runs; --tile applies "
+                         "to it): the hopping term, D or D^+ at mass m_f")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--cg-full", action="store_true",
                     help="also run the three CGs on the benchmark lattice (minutes)")
@@ -557,8 +560,8 @@ def main():
     from paper_2112_01852_gb300.lattice import Lattice
     cuda_build.build()
 
-    if not args.main_only and (args.prec != "f32" or args.nrhs != 1):
-        ap.error("--prec and --nrhs apply to --main-only runs")
+    if not args.main_only and (args.prec != "f32" or args.nrhs != 1 or args.op != "dhop"):
+        ap.error("--prec, --nrhs and --op apply to --main-only runs")
     NR = args.nrhs
     prec = dw.DW_F16 if args.prec == "f16" else dw.DW_F32
     V4 = int(np.prod(DIMS))
@@ -575,19 +578,28 @@ def main():
     x = lat.pack(psi)
     y = lat.empty(NR)
     tiles = {}
+    main_op = {"dhop": dw.DW_OP_DHOP, "d": dw.DW_OP_D, "ddag": dw.DW_OP_DDAG}[args.op]
     if args.tile:
         tv = [int(v) for v in args.tile.split(",")] + [0, 0, 1][len(args.tile.split(",")) - 2:]
         spt, tx, var, zb, sg = tv[:5]
-        lat.set_tile(dw.DW_OP_DHOP, spt, tx, var, nrhs=NR, zblk=zb, sgrp=sg)
-        tiles[dw.DW_OP_DHOP] = (spt, tx, var, zb, sg)
+        lat.set_tile(main_op, spt, tx, var, nrhs=NR, zblk=zb, sgrp=sg)
+        tiles[main_op] = (spt, tx, var, zb, sg)
     else:
-        tiles[dw.DW_OP_DHOP] = lat.tune(dw.DW_OP_DHOP, NR)
+        tiles[main_op] = lat.tune(main_op, NR)
     if not args.main_only:
         for op in (dw.DW_OP_D, dw.DW_OP_DDAG):
             tiles[op] = lat.tune(op, 1)
 
-    def dhop():
-        dw.dw_apply_Dhop(lat.handle, y.data_ptr(), x.data_ptr(), NR, sh)
+    mfs = [MF] * NR
+    if main_op == dw.DW_OP_DHOP:
+        def dhop():
+            dw.dw_apply_Dhop(lat.handle, y.data_ptr(), x.data_ptr(), NR, sh)
+    elif main_op == dw.DW_OP_D:  # profiling runs of the other operators (--main-only)
+        def dhop():
+            dw.dw_apply_D(lat.handle, y.data_ptr(), x.data_ptr(), mfs, NR, sh)
+    else:
+        def dhop():
+            dw.dw_apply_Ddag(lat.handle, y.data_ptr(), x.data_ptr(), mfs, NR, sh)
 
     # warm-up and timed region (barrier + synchronize on both sides)
     for _ in range(args.warmup):
@@ -610,7 +622,7 @@ def main():
     _barrier(ws)
     clocks = sampler.stop()
     ms, sites_per_s = aggregate(ws, e0.elapsed_time(e1) / args.steps, V5 * NR)
-    gflops = FLOP_DHOP * sites_per_s / 1e9
+    gflops = (FLOP_DHOP if main_op == dw.DW_OP_DHOP else FLOP_D_MOBIUS) * sites_per_s / 1e9
 
     # roofline of the Dhop kernel (one launch per step)
     peak, peak_kind = _peaks()
@@ -625,14 +637,16 @@ def main():
         "dtype": "f32", "data": "synthetic", "config": _config(),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": recorded_traffic(tiles[dw.DW_OP_DHOP], DIMS, LS),
+                     "traffic": (recorded_traffic(tiles[dw.DW_OP_DHOP], DIMS, LS)
+                                 if main_op == dw.DW_OP_DHOP else None),
                      "peak_source": peak_kind,
                      "bytes_per_site": bps, "sites_per_launch": V5 * NR},
         "gpu_launches": args.steps,
         "clocks": clocks,
-        "tile": tiles[dw.DW_OP_DHOP],
+        "tile": tiles[main_op],
     }
     if args.main_only or args.layout != "spin_pair":
+        line["op"] = args.op
         line["layout"] = args.layout
         line["dtype"] = "f16" if prec == dw.DW_F16 else "f32"
         line["config"]["nrhs"] = NR

@@ -252,8 +252,9 @@ int dw_solve_eo(dw_lattice *lat, void *x, const void *eta, const double *mf, int
  * 128 registers per thread; 6 = variant 4 with the tile's 32-site blocks of
  * the (x, y) plane and the block on either side bulk-copied into shared memory,
  * the x and y hops read there (needs Lx <= 32, Lx*Ly a multiple of 32, tx
- * dividing Lx*Ly, DW_OP_DHOP / DW_OP_DHOP_DAG only; its bounded wait reports
- * through dw_device_status); 7 = variant 6 with one CTA walking all tiles of
+ * dividing Lx*Ly, DW_OP_DHOP / DW_OP_DHOP_DAG / DW_OP_D, where D also stages
+ * the fifth-dimension neighbours of the CTA's slices and reads its local term
+ * there; its bounded wait reports through dw_device_status); 7 = variant 6 with one CTA walking all tiles of
  * its (z, t) plane, the blocks kept in a ring so that each is copied once per
  * plane (same conditions); 8 = FP16 storage only: the hopping term with its
  * SU(3) x half-spinor products on the tensor cores (mma.sync m16n8k16), Lx
@@ -323,7 +324,7 @@ int dw_set_complex_layout(dw_lattice *lat, int interleaved);
 
 /*
  * Bound of the first wait of each step of the row-staged stencil variants
- * (6, 7, 8) on this lattice: polls >= 0 lets that wait give up after `polls`
+ * (6, 7) on this lattice: polls >= 0 lets that wait give up after `polls`
  * polls of the barrier, -1 (the default) restores the built-in bound of about a
  * second.  A wait that gives up sets the lattice's status word (reported by
  * dw_device_status, and by dw_cg_solve / dw_solve_eo as DW_ERR_TIMEOUT); the

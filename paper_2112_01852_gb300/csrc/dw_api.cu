@@ -120,7 +120,7 @@ bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
   if (t.sgrp < 1 || (lat->Ls / t.spt) % t.sgrp || (op == OP_DDAG && t.sgrp != 1)) return false;
   if ((t.variant == 6 || t.variant == 7) &&
       (!rows_variant_ok(op, lat->dims[0], lat->dims[1], t.tx) ||
-       rows_smem_bytes(t.tx, lat->Ls / t.sgrp, prec) > 227 * 1024))
+       rows_smem_bytes(t.tx, lat->Ls / t.sgrp, prec, op) > 227 * 1024))
     return false;
   const long long threads = (long long)t.tx * (lat->Ls / t.spt / t.sgrp);
   return threads <= 1024 && threads <= dslash_max_threads(prec, op, t.spt, t.variant);
@@ -409,7 +409,7 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
     return fail(DW_ERR_ARG,
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d sgrp=%d for Ls=%d Lz=%d (slices "
                 "per thread must divide Ls, tx a multiple of 32, variant 0..8 (6, 7: Lx <= 32, "
-                "Lx*Ly a multiple of 32, Dhop only; 8: FP16 Dhop, Lx even, Ls a multiple of 4 up to 16, spt 1, tx 32, "
+                "Lx*Ly a multiple of 32, Dhop, Dhop^+ and D only; 8: FP16 Dhop, Lx even, Ls a multiple of 4 up to 16, spt 1, tx 32, "
                 "sgrp 1), zblk dividing Lz, sgrp dividing Ls/spt and 1 for D^+, CTA within "
                 "the kernel's limits)",
                 spt, tx, variant, zblk, sgrp, lat->Ls, lat->dims[2]);

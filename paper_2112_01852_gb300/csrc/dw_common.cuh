@@ -214,14 +214,16 @@ constexpr int kNumVariants = 9;
 // whole blocks (Lx Ly a multiple of 32), tiles of whole blocks that tile the
 // plane, the hopping term alone (Dhop, Dhop^+) and no t halos.
 inline bool rows_variant_ok(int op, int Lx, int Ly, int tx) {
-  return (op == OP_DHOP || op == OP_DHOP_DAG) && Lx <= 32 && (Lx * Ly) % 32 == 0 &&
-         tx % 32 == 0 && tx <= Lx * Ly && (Lx * Ly) % tx == 0;
+  return (op == OP_DHOP || op == OP_DHOP_DAG || op == OP_D) && Lx <= 32 &&
+         (Lx * Ly) % 32 == 0 && tx % 32 == 0 && tx <= Lx * Ly && (Lx * Ly) % tx == 0;
 }
 // Dynamic shared memory of variants 6 and 7: the barrier, then R + 2 rows
 // (y0-1 .. y0+R, or the ring slots) of the CTA's nsl slices at precision
-// `prec` (24 reals per site).
-inline size_t rows_smem_bytes(int tx, int nsl, int prec) {
-  return 128 + (size_t)(tx / 32 + 2) * nsl * 24 * 32 * prec_real_bytes(prec);
+// `prec` (24 reals per site); D (op OP_D) stages two more slices per row, the
+// s-neighbours of the CTA's slice range.
+inline size_t rows_smem_bytes(int tx, int nsl, int prec, int op) {
+  const int nss = nsl + (op == OP_D ? 2 : 0);
+  return 128 + (size_t)(tx / 32 + 2) * nss * 24 * 32 * prec_real_bytes(prec);
 }
 
 // The error of the last stencil launch that failed on this thread (the launch

@@ -488,16 +488,29 @@ __device__ __forceinline__ void half_axpby(Half<V2> &o, V2 a, const Half<V2> &x,
 //   a neighbour index that leaves [0, Ls) wraps and carries -mf.
 // Calls f(j, v) with the spinor of slice s0 + j.  Each half spinor is loaded
 // once: 2 (SPT + 1) half-spinor loads for SPT slices.
-template <class P, bool KDAG, int SPT, class Fn>
+// HINT: the L2 policy of the loads (HINT_KEEP / HINT_DROP as for the hopping
+// term), or HINT_SMEM: F holds a staged copy of a slice range with both
+// neighbours of the range, slice s at index s - s0 + so (no wrap there); the
+// -mf factors still follow the global slice s and the global Ls.
+template <class P, bool KDAG, int SPT, int HINT = HINT_NONE, class Fn>
 __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int Ls,
                                         typename P::C A, typename P::C B,
-                                        typename P::C mf, Fn &&f) {
+                                        typename P::C mf, Fn &&f, int so = 0) {
   using C = typename P::C;
   using V2 = typename Pair<P>::type;
+  constexpr bool STG = (HINT == HINT_SMEM);
+  const unsigned long long pol = l2_policy<HINT>();
   // K: the upper half comes from s-1 (carried), the lower from s+1 (loaded ahead);
   // K^+: the other way round.
   const int carry_half = KDAG ? 1 : 0;
   const int ahead_half = KDAG ? 0 : 1;
+  // (shared memory takes plain loads: the read-only global path faults there)
+  auto ld = [&](Half<V2> &h, int s, int half) {
+    if constexpr (HINT == HINT_NONE)
+      F.load_half(h, x4, s, half);
+    else
+      F.template load_half_h<HINT>(h, x4, s, half, pol);
+  };
   Half<V2> prev, cur_ahead;
   C fp = 1;
   {
@@ -506,22 +519,22 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
       sp = Ls - 1;
       fp = -mf;
     }
-    F.load_half(prev, x4, sp, carry_half);
-    F.load_half(cur_ahead, x4, s0, ahead_half);
+    ld(prev, STG ? so - 1 : sp, carry_half);
+    ld(cur_ahead, STG ? so : s0, ahead_half);
   }
   const V2 vA = bc<V2>(A);
 #pragma unroll
   for (int j = 0; j < SPT; ++j) {
     const int s = s0 + j;
     Half<V2> cur_carry, next_ahead;
-    F.load_half(cur_carry, x4, s, carry_half);
+    ld(cur_carry, STG ? so + j : s, carry_half);
     int sn = s + 1;
     C fn = 1;
     if (sn == Ls) {
       sn = 0;
       fn = -mf;
     }
-    F.load_half(next_ahead, x4, sn, ahead_half);
+    ld(next_ahead, STG ? so + j + 1 : sn, ahead_half);
     Spinor<V2> v;
     Half<V2> &vc = KDAG ? v.lo : v.up;
     Half<V2> &va = KDAG ? v.up : v.lo;
@@ -535,12 +548,15 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
 
 // One hop direction: acc[j] += (1 + S g_mu) W psi'(y4, s0 + j) for every j,
 // where W = U_mu(l4) (ADJ = false) or U_mu(l4)^+ (ADJ = true) and psi' is psi
-// itself (PHI = false) or phi = (b + cK) psi (PHI = true).
+// itself (PHI = false) or phi = (b + cK) psi (PHI = true).  With PHI and
+// HINT_SMEM, F is a staged slice range (roll_5d's STG form; `so` the index of
+// global slice s0 there).
 template <class P, int MU, int S, bool ADJ, bool PHI, bool FIRST, int SPT, int HINT = HINT_NONE>
 __device__ __forceinline__ void hop_dir(SpinorP<P> (&acc)[SPT],
                                         const Field<P> &F, const typename P::vec *gauge,
                                         typename P::C lsign, int y4, int l4, int s0, int Ls,
-                                        typename P::C b, typename P::C c, typename P::C mf) {
+                                        typename P::C b, typename P::C c, typename P::C mf,
+                                        int so = 0) {
   using C = typename P::C;
   C U[18];
   load_link<P>(U, gauge, MU, l4, lsign);
@@ -551,7 +567,10 @@ __device__ __forceinline__ void hop_dir(SpinorP<P> (&acc)[SPT],
     reconstruct<MU, S, FIRST>(acc[j], w);
   };
   if constexpr (PHI) {
-    roll_5d<P, false, SPT>(F, y4, s0, Ls, b, c, mf, body);
+    // (the L2 eviction hints of the hopping term made D slower: 2.06 -> 2.34 ms
+    // at 32^3 x 64 x 12; its global loads keep the default policy)
+    roll_5d<P, false, SPT, HINT == HINT_SMEM ? HINT_SMEM : HINT_NONE>(F, y4, s0, Ls, b, c, mf,
+                                                                    body, so);
   } else {
     const unsigned long long pol = l2_policy<HINT>();
 #pragma unroll
@@ -561,6 +580,52 @@ __device__ __forceinline__ void hop_dir(SpinorP<P> (&acc)[SPT],
       F.template load_half_h<HINT>(v.lo, y4, s0 + j, 1, pol);
       body(j, v);
     }
+  }
+}
+
+// The D epilogue at output site xo, slices s0 .. s0+SPT-1:
+//   out = alpha psi + beta K psi + h acc   (h = hscale, -1/2 for D_W),
+// psi read from Fo at index io (STG: a staged slice range holding slice s0 at
+// index so, roll_5d's STG form; own false: no local term).  Adds |out|^2 to
+// nsq when `norm`.
+template <class P, int SPT, bool STG>
+__device__ __forceinline__ void d_epilogue(const SpinorP<P> (&acc)[SPT], typename P::vec *out,
+                                           int xo, const Field<P> &Fo, bool own, int io, int so,
+                                           int s0, int Ls, typename P::C alpha,
+                                           typename P::C beta, typename P::C mf,
+                                           typename Pair<P>::type h, bool norm, double &nsq) {
+  using C = typename P::C;
+  using V2 = typename Pair<P>::type;
+  constexpr int NPV = 24 / P::R;
+  auto emit = [&](int j, const Spinor<V2> &v) {
+    Spinor<V2> o;
+    C ss = 0;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      o.up.re[cc] = p_fma(h, acc[j].up.re[cc], v.up.re[cc]);
+      o.up.im[cc] = p_fma(h, acc[j].up.im[cc], v.up.im[cc]);
+      o.lo.re[cc] = p_fma(h, acc[j].lo.re[cc], v.lo.re[cc]);
+      o.lo.im[cc] = p_fma(h, acc[j].lo.im[cc], v.lo.im[cc]);
+      if (norm) {
+        ss += o.up.re[cc].x * o.up.re[cc].x + o.up.re[cc].y * o.up.re[cc].y;
+        ss += o.up.im[cc].x * o.up.im[cc].x + o.up.im[cc].y * o.up.im[cc].y;
+        ss += o.lo.re[cc].x * o.lo.re[cc].x + o.lo.re[cc].y * o.lo.re[cc].y;
+        ss += o.lo.im[cc].x * o.lo.im[cc].x + o.lo.im[cc].y * o.lo.im[cc].y;
+      }
+    }
+    nsq += (double)ss;
+    store_spinor<P>(out + site_off(xo, s0 + j, Ls, NPV), kPlaneStride, o);
+  };
+  if (own) {
+    roll_5d<P, false, SPT, STG ? HINT_SMEM : HINT_NONE>(Fo, io, s0, Ls, alpha, beta, mf, emit,
+                                                        so);
+  } else {
+    Spinor<V2> zero_v;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+      zero_v.up.re[cc] = zero_v.up.im[cc] = zero_v.lo.re[cc] = zero_v.lo.im[cc] = bc<V2>(C(0));
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) emit(j, zero_v);
   }
 }
 
@@ -1147,6 +1212,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   SpinorP<P> acc[SPT];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t smem_used = 0;
+  double nsq = 0.0;     // OP_D: |out|^2 of this thread's output sites
+  bool stored = false;  // OP_D on the rows path: stored inside its loop
 
   int nb[8];   // neighbours in the order t+, t-, z+, z-, y+, y-, x+, x-
   int lsg[8];  // boundary sign of the link each of those hops uses
@@ -1200,9 +1267,15 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     // blocks in a ring of R + 2 slots (block v in slot (v + 1) mod (R + 2)):
     // each step copies only its R new blocks, the two shared with the previous
     // tile stay, and the next step's t+ blocks are prefetched into L2.
+    // D (PHI): phi = (b + cK) psi needs the upper spins of the slice below the
+    // CTA's range and the lower spins of the one above (wrapped in s): each
+    // staged block holds nsl + 2 slices, those two halves at its ends, and the
+    // D epilogue takes its own-site psi from the staged blocks as well.
     constexpr bool RING = (VAR == 7);
     constexpr int NPV = 24 / P::R;
+    constexpr int EDGE = PHI ? 1 : 0;
     const int nsl = nchunk * SPT;  // slices of this CTA
+    const int nss = nsl + 2 * EDGE;  // staged slices per block
     const int sbase = sg * nsl;
     const int R = tx / 32;
     const int Lx = p.L[0];
@@ -1210,13 +1283,16 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     const int NR = R + 2;  // row slots
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw);
     vec *rows = reinterpret_cast<vec *>(smem_raw + 128);
-    const int row_vecs = nsl * NPV * 32;
-    const unsigned row_bytes = (unsigned)(row_vecs * sizeof(vec));
+    const int row_vecs = nss * NPV * 32;
+    const unsigned row_bytes = (unsigned)(nsl * NPV * 32 * sizeof(vec));
+    const unsigned half_bytes = (unsigned)((NPV / 2) * 32 * sizeof(vec));
+    const unsigned blk_bytes = row_bytes + 2 * EDGE * half_bytes;
+    const int s_below = sbase == 0 ? Ls - 1 : sbase - 1;  // PHI: the edge slices
+    const int s_above = sbase + nsl == Ls ? 0 : sbase + nsl;
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     const int plane_base = x4 - in_plane;  // x4 of site 0 of the plane
     const int plane_blk = plane_base >> 5;  // block of row 0 of the plane
     const int steps = RING ? (Lx * p.L[1]) / tx : 1;
-    const C zero = C(0);  // the hopping term alone: no (b + cK) combination
     const int sl = (int)threadIdx.y * SPT;  // = s0 - sbase
     if (leader) mbar_init(bar, 1);
     __syncthreads();
@@ -1230,13 +1306,19 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         const int first = (RING && k > 0) ? y0 + 1 : y0 - 1;
         const int n = (RING && k > 0) ? R : R + 2;
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        mbar_expect_tx(bar, row_bytes * (unsigned)n);
+        mbar_expect_tx(bar, blk_bytes * (unsigned)n);
         for (int r = 0; r < n; ++r) {
           const int v = first + r;  // virtual block, -1 .. nblk
           const int y = v < 0 ? v + nblk : (v >= nblk ? v - nblk : v);
           const int slot = RING ? (v + 1) % NR : r;
-          const vec *src = F.base + ((long long)(plane_blk + y) * Ls + sbase) * NPV * 32;
-          bulk_g2s(rows + (size_t)slot * row_vecs, src, row_bytes, bar);
+          const vec *blk = F.base + (long long)(plane_blk + y) * Ls * NPV * 32;
+          vec *dst = rows + (size_t)slot * row_vecs;
+          bulk_g2s(dst + EDGE * NPV * 32, blk + (long long)sbase * NPV * 32, row_bytes, bar);
+          if (PHI) {
+            bulk_g2s(dst, blk + (long long)s_below * NPV * 32, half_bytes, bar);
+            bulk_g2s(dst + (nss - 1) * NPV * 32 + (NPV / 2) * 32,
+                     blk + (long long)s_above * NPV * 32 + (NPV / 2) * 32, half_bytes, bar);
+          }
         }
         if (RING && k + 1 < steps) {
           // the t+ neighbours are the first touch of their plane (read from
@@ -1252,17 +1334,16 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         }
       }
       const Hops H(p, xs);
-      hop_dir<P, 3, SF, false, false, true, SPT, HINT_KEEP>(
-          acc, F, gauge, (C)H.sign<3, true>(p), H.nb<3, true>(p), xs, s0, Ls, zero, zero, zero);
-      hop_dir<P, 3, SB, true, false, false, SPT, HINT_DROP>(
+      hop_dir<P, 3, SF, false, PHI, true, SPT, HINT_KEEP>(
+          acc, F, gauge, (C)H.sign<3, true>(p), H.nb<3, true>(p), xs, s0, Ls, b, c, mf);
+      hop_dir<P, 3, SB, true, PHI, false, SPT, HINT_DROP>(
           acc, F, gauge, (C)H.sign<3, false>(p), H.nb<3, false>(p), H.nb<3, false>(p), s0, Ls,
-          zero, zero, zero);
-      hop_dir<P, 2, SF, false, false, false, SPT>(acc, F, gauge, (C)H.sign<2, true>(p),
-                                                  H.nb<2, true>(p), xs, s0, Ls, zero, zero,
-                                                  zero);
-      hop_dir<P, 2, SB, true, false, false, SPT>(acc, F, gauge, (C)H.sign<2, false>(p),
-                                                 H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls,
-                                                 zero, zero, zero);
+          b, c, mf);
+      hop_dir<P, 2, SF, false, PHI, false, SPT>(acc, F, gauge, (C)H.sign<2, true>(p),
+                                                H.nb<2, true>(p), xs, s0, Ls, b, c, mf);
+      hop_dir<P, 2, SB, true, PHI, false, SPT>(acc, F, gauge, (C)H.sign<2, false>(p),
+                                               H.nb<2, false>(p), H.nb<2, false>(p), s0, Ls,
+                                               b, c, mf);
       // p.wait_polls >= 0 bounds the first wait by that many polls (0: give up
       // at once, which exercises the timeout report); the second bounded wait
       // still lets the copies in flight land before the slots are read
@@ -1270,13 +1351,13 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         atomicExch(p.status, 1);
         mbar_wait(bar, (unsigned)k & 1u);  // one more bounded wait for the copies in flight
       }
-      Field<P> S;  // the staged rows, addressed as blocks of 32 sites x nsl slices
+      Field<P> S;  // the staged rows, addressed as blocks of 32 sites x nss slices
       S.base = rows;
       S.V4 = 0;
-      S.Ls = nsl;
+      S.Ls = nss;
       // staged index of the in-plane site q (virtual: q < 0 and q >= Lx Ly are
       // the neighbouring rows across the periodic y edge, in blocks -1, nblk)
-      int iyp, iym, ixp, ixm;
+      int iyp, iym, ixp, ixm, iat;
       if constexpr (!GLX) {  // Lx = 32: a block is one x row: the row's slot and the lane
         const int ry = (ip >> 5) - y0;  // row of this site in the tile
         const int xl = ip & 31;
@@ -1287,6 +1368,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         iym = sdn * 32 + xl;
         ixp = sat * 32 + ((xl + 1) & 31);
         ixm = sat * 32 + ((xl + 31) & 31);
+        iat = sat * 32 + xl;
       } else {
         auto sidx = [&](int q) {
           const int v = (q + 32) / 32 - 1;  // floor(q / 32) for q >= -32
@@ -1298,26 +1380,37 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         iym = sidx(ip - Lx);
         ixp = sidx(xc == Lx - 1 ? ip - (Lx - 1) : ip + 1);
         ixm = sidx(xc == 0 ? ip + (Lx - 1) : ip - 1);
+        iat = sidx(ip);
       }
-      hop_dir<P, 1, SF, false, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<1, true>(p), iyp, xs, sl, nsl, zero, zero, zero);
-      hop_dir<P, 1, SB, true, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<1, false>(p), iym, H.nb<1, false>(p), sl, nsl, zero,
-          zero, zero);
-      hop_dir<P, 0, SF, false, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<0, true>(p), ixp, xs, sl, nsl, zero,
-          zero, zero);
-      hop_dir<P, 0, SB, true, false, false, SPT, HINT_SMEM>(
-          acc, S, gauge, (C)H.sign<0, false>(p), ixm, H.nb<0, false>(p),
-          sl, nsl, zero, zero, zero);
-      if (RING) {
+      // staged slices: the hopping term alone addresses slice sl of nsl; D
+      // passes the global slice and Ls (for the -mf factors of K) and the
+      // staged index sl + 1 of slice s0
+      const int hs = PHI ? s0 : sl, hL = PHI ? Ls : nsl;
+      hop_dir<P, 1, SF, false, PHI, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<1, true>(p), iyp, xs, hs, hL, b, c, mf, sl + EDGE);
+      hop_dir<P, 1, SB, true, PHI, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<1, false>(p), iym, H.nb<1, false>(p), hs, hL, b, c, mf,
+          sl + EDGE);
+      hop_dir<P, 0, SF, false, PHI, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<0, true>(p), ixp, xs, hs, hL, b, c, mf, sl + EDGE);
+      hop_dir<P, 0, SB, true, PHI, false, SPT, HINT_SMEM>(
+          acc, S, gauge, (C)H.sign<0, false>(p), ixm, H.nb<0, false>(p), hs, hL, b, c, mf,
+          sl + EDGE);
+      if constexpr (OP == OP_D) {
+        // the local term from the staged own site (the launch requires own = in)
+        d_epilogue<P, SPT, true>(acc, out, xs, S, true, iat, sl + 1, s0, Ls, alpha, beta, mf,
+                                 bc<V2>((C)p.hscale), p.norm_partials != nullptr, nsq);
+        stored = true;
+      } else if (RING) {
 #pragma unroll
         for (int j = 0; j < SPT; ++j)
           store_spinor<P>(out + F.site(s0 + j, xs), kPlaneStride, acc[j]);
-        __syncthreads();  // every thread is done with the slots the next step refills
       }
+      if (RING) __syncthreads();  // every thread is done with the slots the next step refills
     }
-    if (RING) return;
+    if constexpr (OP != OP_D) {
+      if (RING) return;
+    }
   } else if constexpr (VAR == 0 || VAR == 4 || VAR == 5) {
     if (active) {
       const Hops H(p, x4);
@@ -1398,39 +1491,9 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   } else if constexpr (OP == OP_D) {
     // out = alpha psi + beta K psi - 1/2 Dhop phi; optionally |out|^2 per CTA
     // (the CG's <p, D^+D p> = |D p|^2, fused here to save a pass over two fields)
-    double nsq = 0.0;
-    auto emit = [&](int j, const Spinor<V2> &v) {
-        Spinor<V2> o;
-        C ss = 0;
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          o.up.re[cc] = p_fma(mhalf, acc[j].up.re[cc], v.up.re[cc]);
-          o.up.im[cc] = p_fma(mhalf, acc[j].up.im[cc], v.up.im[cc]);
-          o.lo.re[cc] = p_fma(mhalf, acc[j].lo.re[cc], v.lo.re[cc]);
-          o.lo.im[cc] = p_fma(mhalf, acc[j].lo.im[cc], v.lo.im[cc]);
-          if (p.norm_partials) {
-            ss += o.up.re[cc].x * o.up.re[cc].x + o.up.re[cc].y * o.up.re[cc].y;
-            ss += o.up.im[cc].x * o.up.im[cc].x + o.up.im[cc].y * o.up.im[cc].y;
-            ss += o.lo.re[cc].x * o.lo.re[cc].x + o.lo.re[cc].y * o.lo.re[cc].y;
-            ss += o.lo.im[cc].x * o.lo.im[cc].x + o.lo.im[cc].y * o.lo.im[cc].y;
-          }
-        }
-        nsq += (double)ss;
-        store(j, o);
-    };
-    if (active) {
-      if (p.own) {
-        roll_5d<P, false, SPT>(Fo, xf, s0, Ls, alpha, beta, mf, emit);
-      } else {
-        Spinor<V2> zero_v;
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          zero_v.up.re[cc] = zero_v.up.im[cc] = zero_v.lo.re[cc] = zero_v.lo.im[cc] = bc<V2>(C(0));
-        }
-#pragma unroll
-        for (int j = 0; j < SPT; ++j) emit(j, zero_v);
-      }
-    }
+    if (active && !stored)
+      d_epilogue<P, SPT, false>(acc, out, xf, Fo, p.own != nullptr, xf, 0, s0, Ls, alpha, beta,
+                                mf, mhalf, p.norm_partials != nullptr, nsq);
     if (p.norm_partials) {
       // fixed-order block sum: warp shuffles, then warp 0 over the warp sums
       __shared__ double warp_sums[32];
@@ -1581,7 +1644,7 @@ template <class P, int OP, int SPT, int VAR>
 size_t dslash_smem(int tx, int nchunk) {
   size_t smem = 0;
   if (VAR == 1) smem += kStages * StageLayout<P, OP == OP_D, SPT>::stage_bytes(tx * nchunk);
-  if (VAR == 6 || VAR == 7) smem += rows_smem_bytes(tx, nchunk * SPT, P::id);
+  if (VAR == 6 || VAR == 7) smem += rows_smem_bytes(tx, nchunk * SPT, P::id, OP);
   if (OP == OP_DDAG) smem += 2 * (size_t)nchunk * 12 * tx * sizeof(typename P::C);  // 6 pairs
   return smem;
 }
@@ -1602,8 +1665,9 @@ int launch_one_k(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t
   q.zblk = zblk;
   q.sgrp = sgrp;
   if (zblk < 1 || p.L[2] % zblk) return -2;
-  if ((VAR == 6 || VAR == 7) &&
-      (!rows_variant_ok(OP, p.L[0], p.L[1], tx) || p.halo_up || p.halo_dn))
+  // (D: the local term is taken from the staged rows, so own must be in)
+  if ((VAR == 6 || VAR == 7) && (!rows_variant_ok(OP, p.L[0], p.L[1], tx) || p.halo_up ||
+                                 p.halo_dn || (OP == OP_D && p.own != p.in)))
     return -2;
   if (q.t_count == 0) {
     q.t_begin = 0;

@@ -141,32 +141,66 @@ def test_row_staged_variant(prec, dims):
     # bit for bit, and within tolerance of the oracle.  Ly = 2 and 1 at Lx = 32,
     # and a plane of one block: the halo blocks repeat blocks of the tile (and
     # the ring wraps within one step); Lx = 24: a block holds a row and a part.
+    # D stages the s-neighbours of each CTA's slice range as well (wrapped in s
+    # with the -m_f factor at sgrp 1, the first and the last slice group), and
+    # takes its local term alpha psi + beta K psi from the staged own site.
     Ls = 4
     U, psi = make_case(dims, Ls, 2, seed=17)
+    mfs = [0.03, 0.2]
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
     lat.load_gauge(U)
     ran = 0
-    for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG):
-        ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.0, 0.0])
+    for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG, dw.DW_OP_D):
+        mf = mfs if op == dw.DW_OP_D else [0.0, 0.0]
+        ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mf)
         for spt in (1, 2):
             lat.set_tile(op, spt, 32, 5)
-            v5 = run_gpu(lat, op, psi)
+            v5 = run_gpu(lat, op, psi, mf=mf)
             for var, tx, sgrp in itertools.product((6, 7), (32, 64, 128), (1, 2, 4)):
                 try:
                     lat.set_tile(op, spt, tx, var, sgrp=sgrp)
                 except dw.DWError as e:
                     assert e.code == dw.DW_ERR_ARG
                     continue
-                got = run_gpu(lat, op, psi)
+                got = run_gpu(lat, op, psi, mf=mf)
                 assert np.array_equal(got, v5), (OP_NAMES[op], spt, tx, var, sgrp)
                 assert max_rel(got, ref) <= TOL[prec]
                 ran += 1
     dw.dw_device_status(lat.handle)
-    assert ran >= 16
+    assert ran >= 24
     for var in (6, 7):
-        with pytest.raises(dw.DWError):  # D is not a hopping-only operator
-            lat.set_tile(dw.DW_OP_D, 1, 32, var)
+        with pytest.raises(dw.DWError):  # D^+ combines all slices of a site after the hops
+            lat.set_tile(dw.DW_OP_DDAG, 1, 32, var)
     lat.close()
+
+
+@pytest.mark.parametrize("variant", [6, 7])
+def test_row_staged_D_in_mixed_cg(variant):
+    # the mixed-precision CG's D pass with a row-staged tile (its |D p|^2 CTA
+    # partials are summed over the steps of a ring CTA): the solve reaches an
+    # oracle-recomputed residual <= 1e-10 in the iterations of the default tile
+    dims, Ls, nrhs = (32, 4, 4, 4), 8, 2
+    U, eta = make_case(dims, Ls, nrhs, seed=23)
+    mfs = [0.1, 0.3]
+    iters = {}
+    for forced in (False, True):
+        lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F64)
+        lat.load_gauge(U)
+        if forced:
+            lat.set_tile(dw.DW_OP_D, 2, 64, variant, nrhs=nrhs, prec=dw.DW_F32, sgrp=2)
+        b = lat.pack(eta)
+        x = lat.empty(nrhs)
+        x.zero_()
+        rc, stats = lat.cg(x, b, mfs, nrhs, tol=1e-10, maxit=2000, mode=dw.DW_F32)
+        assert rc == dw.DW_OK and all(st.converged for st in stats)
+        xs = lat.unpack(x, nrhs)
+        lat.close()
+        Ax = oracle.dwdagdw(xs, U, dims, Ls, 1.8, 1.5, 0.5, mfs, BC)
+        for r in range(nrhs):
+            rel = np.linalg.norm((eta[r] - Ax[r]).ravel()) / np.linalg.norm(eta[r].ravel())
+            assert rel <= 1e-10, (forced, r, rel)
+        iters[forced] = [st.iters for st in stats]
+    assert all(abs(a - b) <= 2 for a, b in zip(iters[True], iters[False])), iters
 
 
 @pytest.mark.parametrize("dims", [(48, 2, 2, 4), (12, 4, 2, 4)], ids=["Lx48", "plane48"])
@@ -184,7 +218,8 @@ def test_row_staged_variant_limits(dims):
     lat.close()
 
 
-@pytest.mark.parametrize("op", [dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG], ids=["Dhop", "Dhop_dag"])
+@pytest.mark.parametrize("op", [dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG, dw.DW_OP_D],
+                         ids=["Dhop", "Dhop_dag", "D"])
 def test_bounded_wait_timeout_is_reported(op):
     # With the first bounded wait of each step limited to zero polls, every
     # row-staged launch gives up that wait: the kernel records the timeout in
@@ -194,7 +229,8 @@ def test_bounded_wait_timeout_is_reported(op):
     # clear.
     dims, Ls = (32, 4, 2, 4), 4
     U, psi = make_case(dims, Ls, 1, seed=19)
-    ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.0])
+    mf = [0.05] if op == dw.DW_OP_D else [0.0]
+    ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, mf)
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F32)
     lat.load_gauge(U)
     with pytest.raises(dw.DWError) as e:
@@ -204,14 +240,14 @@ def test_bounded_wait_timeout_is_reported(op):
         lat.set_tile(op, 1, 32, var)
         dw.dw_device_status(lat.handle)
         dw.dw_set_wait_polls(lat.handle, 0)
-        got = run_gpu(lat, op, psi)
+        got = run_gpu(lat, op, psi, mf=mf)
         with pytest.raises(dw.DWError) as e:
             dw.dw_device_status(lat.handle)
         assert e.value.code == dw.DW_ERR_TIMEOUT, var
         dw.dw_device_status(lat.handle)  # read and cleared: no second report
         assert max_rel(got, ref) <= TOL[dw.DW_F32], var
         dw.dw_set_wait_polls(lat.handle, -1)
-        got = run_gpu(lat, op, psi)
+        got = run_gpu(lat, op, psi, mf=mf)
         dw.dw_device_status(lat.handle)
         assert max_rel(got, ref) <= TOL[dw.DW_F32], var
     lat.close()
