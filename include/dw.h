@@ -263,8 +263,9 @@ int dw_solve_eo(dw_lattice *lat, void *x, const void *eta, const double *mf, int
  * number of z-blocks of the CTA traversal order (planes are visited block by
  * block, t inside a block; zblk divides Lz; 0 in dw_set_tile = automatic), and
  * sgrp, the number of CTAs that share one tile of tx sites: each holds
- * Ls/(spt sgrp) slice groups (sgrp divides Ls/spt; DW_OP_DDAG needs sgrp = 1,
- * its slice-group edges meet in shared memory).  Smaller CTAs let more of them
+ * Ls/(spt sgrp) slice groups (sgrp divides Ls/spt; DW_OP_DDAG combines the
+ * edges of neighbouring slice groups, so its sgrp CTAs run as one thread-block
+ * cluster and sgrp is at most 8).  Smaller CTAs let more of them
  * fit on an SM when registers limit the occupancy.
  *
  * dw_set_tile pins the tile used for operator `op` (DW_OP_DHOP .. DW_OP_DDAG)

@@ -117,7 +117,7 @@ bool tile_valid(const dw_lattice *lat, int prec, int op, TileConfig t) {
     return prec == DW_F16 && !lat->cplx && tc_variant_ok(op, lat->dims[0], lat->Ls) &&
            t.spt == 1 && t.tx == 32 && t.sgrp == 1 && t.zblk >= 1 && lat->dims[2] % t.zblk == 0;
   if (t.zblk < 1 || lat->dims[2] % t.zblk) return false;
-  if (t.sgrp < 1 || (lat->Ls / t.spt) % t.sgrp || (op == OP_DDAG && t.sgrp != 1)) return false;
+  if (t.sgrp < 1 || (lat->Ls / t.spt) % t.sgrp || (op == OP_DDAG && t.sgrp > 8)) return false;
   if ((t.variant == 6 || t.variant == 7) &&
       (!rows_variant_ok(op, lat->dims[0], lat->dims[1], t.tx) ||
        rows_smem_bytes(t.tx, lat->Ls / t.sgrp, prec, op) > 227 * 1024))
@@ -410,7 +410,7 @@ int dw_set_tile(dw_lattice *lat, int op, int prec, int nrhs, int spt, int tx, in
                 "invalid tile spt=%d tx=%d variant=%d zblk=%d sgrp=%d for Ls=%d Lz=%d (slices "
                 "per thread must divide Ls, tx a multiple of 32, variant 0..8 (6, 7: Lx <= 32, "
                 "Lx*Ly a multiple of 32, Dhop, Dhop^+ and D only; 8: FP16 Dhop, Lx even, Ls a multiple of 4 up to 16, spt 1, tx 32, "
-                "sgrp 1), zblk dividing Lz, sgrp dividing Ls/spt and 1 for D^+, CTA within "
+                "sgrp 1), zblk dividing Lz, sgrp dividing Ls/spt and at most 8 for D^+, CTA within "
                 "the kernel's limits)",
                 spt, tx, variant, zblk, sgrp, lat->Ls, lat->dims[2]);
   lat->tuned[std::make_tuple(prec, op, nrhs)] = t;

@@ -19,6 +19,7 @@
 // Dhop uses S = -1 forward and S = +1 backward; Dhop^+ the opposite.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "dw_common.cuh"
@@ -1382,10 +1383,10 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         ixm = sidx(xc == 0 ? ip + (Lx - 1) : ip - 1);
         iat = sidx(ip);
       }
-      // staged slices: the hopping term alone addresses slice sl of nsl; D
-      // passes the global slice and Ls (for the -mf factors of K) and the
-      // staged index sl + 1 of slice s0
-      const int hs = PHI ? s0 : sl, hL = PHI ? Ls : nsl;
+      // staged slices: the hopping term alone addresses slice sl + EDGE of the
+      // nss staged ones; D passes the global slice and Ls (for the -mf factors
+      // of K) and the staged index sl + 1 of slice s0
+      const int hs = PHI ? s0 : sl + EDGE, hL = PHI ? Ls : nss;
       hop_dir<P, 1, SF, false, PHI, false, SPT, HINT_SMEM>(
           acc, S, gauge, (C)H.sign<1, true>(p), iyp, xs, hs, hL, b, c, mf, sl + EDGE);
       hop_dir<P, 1, SB, true, PHI, false, SPT, HINT_SMEM>(
@@ -1515,19 +1516,28 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     // OP_DDAG: out = alpha psi + beta K^+ psi - 1/2 (b + c K^+) Dhop^+ psi.
     // K^+ acc needs the upper spins of slice s+1 and the lower spins of s-1;
     // at chunk edges they come from the neighbouring chunk through shared memory.
+    // With sgrp > 1 the sgrp CTAs of a tile form one thread-block cluster (rank
+    // = slice group) and the edges of a neighbouring group are read from that
+    // CTA's shared memory (distributed shared memory, after a cluster barrier).
     V2 *sm_up = reinterpret_cast<V2 *>(smem_raw + smem_used);  // [nchunk][6][tx]
     V2 *sm_lo = sm_up + (size_t)nchunk * 6 * tx;    // [nchunk][6][tx]
     const int t = threadIdx.x;
+    const int lch = threadIdx.y;          // this CTA's slot of the chunk
+    const int tch = nchunk * p.sgrp;      // chunks of the whole tile
+    const bool clustered = p.sgrp > 1;
     if (active) {
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) {
-        sm_up[((size_t)chunk * 6 + 2 * cc) * tx + t] = acc[0].up.re[cc];
-        sm_up[((size_t)chunk * 6 + 2 * cc + 1) * tx + t] = acc[0].up.im[cc];
-        sm_lo[((size_t)chunk * 6 + 2 * cc) * tx + t] = acc[SPT - 1].lo.re[cc];
-        sm_lo[((size_t)chunk * 6 + 2 * cc + 1) * tx + t] = acc[SPT - 1].lo.im[cc];
+        sm_up[((size_t)lch * 6 + 2 * cc) * tx + t] = acc[0].up.re[cc];
+        sm_up[((size_t)lch * 6 + 2 * cc + 1) * tx + t] = acc[0].up.im[cc];
+        sm_lo[((size_t)lch * 6 + 2 * cc) * tx + t] = acc[SPT - 1].lo.re[cc];
+        sm_lo[((size_t)lch * 6 + 2 * cc + 1) * tx + t] = acc[SPT - 1].lo.im[cc];
       }
     }
-    __syncthreads();
+    if (clustered)
+      cooperative_groups::this_cluster().sync();
+    else
+      __syncthreads();
     // fused CG residual update (p.rs): r_s at FP64 for FP64 operators, else FP32
     using PR = typename std::conditional<std::is_same<C, double>::value, F64, F32>::type;
     using rvec = typename PR::vec;
@@ -1535,10 +1545,17 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     constexpr int RVPQ = 4 / PR::R;
     double rsq = 0.0;
     if (active) {
-      const int cn = (chunk + 1 == nchunk) ? 0 : chunk + 1;
-      const int cp = (chunk == 0) ? nchunk - 1 : chunk - 1;
-      const V2 fn = bc<V2>((chunk + 1 == nchunk) ? -mf : C(1));
+      const int gn = (chunk + 1 == tch) ? 0 : chunk + 1;  // neighbouring chunks of the tile
+      const int gp = (chunk == 0) ? tch - 1 : chunk - 1;
+      const V2 fn = bc<V2>((chunk + 1 == tch) ? -mf : C(1));
       const V2 fp = bc<V2>((chunk == 0) ? -mf : C(1));
+      const int cn = gn % nchunk, cp = gp % nchunk;  // their slots in their CTA
+      const V2 *up_src = sm_up, *lo_src = sm_lo;
+      if (clustered) {
+        auto cl = cooperative_groups::this_cluster();
+        if (gn / nchunk != sg) up_src = cl.map_shared_rank(sm_up, (unsigned)(gn / nchunk));
+        if (gp / nchunk != sg) lo_src = cl.map_shared_rank(sm_lo, (unsigned)(gp / nchunk));
+      }
       const V2 mb = bc<V2>((C)p.hscale * b), mc = bc<V2>((C)p.hscale * c);
       auto emit = [&](int j, const Spinor<V2> &v) {
         Spinor<V2> o;
@@ -1550,15 +1567,15 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
             kur = acc[(j + 1 < SPT) ? j + 1 : 0].up.re[cc];
             kui = acc[(j + 1 < SPT) ? j + 1 : 0].up.im[cc];
           } else {
-            kur = p_mul(fn, sm_up[((size_t)cn * 6 + 2 * cc) * tx + t]);
-            kui = p_mul(fn, sm_up[((size_t)cn * 6 + 2 * cc + 1) * tx + t]);
+            kur = p_mul(fn, up_src[((size_t)cn * 6 + 2 * cc) * tx + t]);
+            kui = p_mul(fn, up_src[((size_t)cn * 6 + 2 * cc + 1) * tx + t]);
           }
           if (j > 0) {
             klr = acc[(j > 0) ? j - 1 : 0].lo.re[cc];
             kli = acc[(j > 0) ? j - 1 : 0].lo.im[cc];
           } else {
-            klr = p_mul(fp, sm_lo[((size_t)cp * 6 + 2 * cc) * tx + t]);
-            kli = p_mul(fp, sm_lo[((size_t)cp * 6 + 2 * cc + 1) * tx + t]);
+            klr = p_mul(fp, lo_src[((size_t)cp * 6 + 2 * cc) * tx + t]);
+            kli = p_mul(fp, lo_src[((size_t)cp * 6 + 2 * cc + 1) * tx + t]);
           }
           o.up.re[cc] = p_fma(mc, kur, p_fma(mb, acc[j].up.re[cc], v.up.re[cc]));
           o.up.im[cc] = p_fma(mc, kui, p_fma(mb, acc[j].up.im[cc], v.up.im[cc]));
@@ -1617,6 +1634,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
         if (tid == 0) p.rs_partials[(long long)rhs * ctas_per_rhs + cta_in_rhs] = v;
       }
     }
+    // the other CTAs of the cluster may still read this CTA's edges
+    if (clustered) cooperative_groups::this_cluster().sync();
   }
 }
 
@@ -1651,8 +1670,11 @@ size_t dslash_smem(int tx, int nchunk) {
 
 template <class P, int OP, int SPT, int VAR, bool CB, bool GLX>
 int launch_one_k(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t st) {
-  // D^+ exchanges slice-group edges through shared memory: one CTA per tile
-  if (sgrp < 1 || (p.Ls / SPT) % sgrp || (OP == OP_DDAG && sgrp != 1)) return -2;
+  // D^+ exchanges slice-group edges through shared memory: the sgrp CTAs of a
+  // tile run as one thread-block cluster (at most 8, the portable size), the
+  // RHS outermost so that a cluster never spans two right-hand sides
+  constexpr bool kClusterOp = (OP == OP_DDAG);
+  if (sgrp < 1 || (p.Ls / SPT) % sgrp || (kClusterOp && sgrp > 8)) return -2;
   // checkerboard launches: register variants only, Lx even, no halos
   if (CB && ((VAR != 0 && VAR != 4 && VAR != 5) || (p.L[0] & 1) || p.halo_up || p.halo_dn))
     return -2;
@@ -1664,6 +1686,7 @@ int launch_one_k(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t
   q.tiles_per_plane = VAR == 7 ? 1 : (plane_sites + tx - 1) / tx;
   q.zblk = zblk;
   q.sgrp = sgrp;
+  if (kClusterOp && sgrp > 1) q.rhs_outer = 1;
   if (zblk < 1 || p.L[2] % zblk) return -2;
   // (D: the local term is taken from the staged rows, so own must be in)
   if ((VAR == 6 || VAR == 7) && (!rows_variant_ok(OP, p.L[0], p.L[1], tx) || p.halo_up ||
@@ -1702,8 +1725,26 @@ int launch_one_k(const DslashParams &p, int tx, int zblk, int sgrp, cudaStream_t
       return -3;
     smem_set = smem;
   }
-  dslash_entry<P, OP, SPT, VAR, CB, GLX>()<<<grid, block, smem, st>>>(q);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (kClusterOp && sgrp > 1) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)sgrp;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelEx(&lc, dslash_entry<P, OP, SPT, VAR, CB, GLX>(), q);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  } else {
+    dslash_entry<P, OP, SPT, VAR, CB, GLX>()<<<grid, block, smem, st>>>(q);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) return 0;
   last_launch_error() = e;
   return -1;

@@ -390,7 +390,7 @@ int tune_cb(dw_lattice *lat, int prec, int op, cudaStream_t st) {
   for (int spt : {1, 2, 3, 4})
     for (int tx : {32, 64, 128})
       for (int sgrp : {1, 2, 3, 4, 6}) {
-        if (lat->Ls % spt || (lat->Ls / spt) % sgrp || (op == OP_DDAG && sgrp != 1)) continue;
+        if (lat->Ls % spt || (lat->Ls / spt) % sgrp || (op == OP_DDAG && sgrp > 8)) continue;
         const TileConfig t{spt, tx, prec == DW_F64 ? 0 : 4, za, sgrp};
         if (tx * (lat->Ls / spt / sgrp) > 1024) continue;
         if (run_dslash_cb(lat, prec, op, lat->stage_out, lat->stage_in, nullptr, 0, 0.0, 0.0,

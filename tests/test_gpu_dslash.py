@@ -111,7 +111,9 @@ def test_slice_groups_equal_one_cta(prec):
     lat = _lattice(dims, Ls, dw.DW_MOBIUS, prec)
     lat.load_gauge(U)
     ran = 0
-    for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG, dw.DW_OP_D):
+    # D^+: the slice groups of a tile form a thread-block cluster and exchange
+    # their edge slices through distributed shared memory (sgrp <= 8)
+    for op in (dw.DW_OP_DHOP, dw.DW_OP_DHOP_DAG, dw.DW_OP_D, dw.DW_OP_DDAG):
         for variant in range(8):
             for spt in (1, 2, 3):
                 try:
@@ -120,7 +122,7 @@ def test_slice_groups_equal_one_cta(prec):
                     continue
                 ref = run_gpu(lat, op, psi, mf=mfs)
                 for sgrp in (2, 3, 4, 6, 12):
-                    if (Ls // spt) % sgrp:
+                    if (Ls // spt) % sgrp or (op == dw.DW_OP_DDAG and sgrp > 8):
                         continue
                     lat.set_tile(op, spt, 32, variant, sgrp=sgrp)
                     got = run_gpu(lat, op, psi, mf=mfs)
@@ -174,11 +176,16 @@ def test_row_staged_variant(prec, dims):
     lat.close()
 
 
-@pytest.mark.parametrize("variant", [6, 7])
-def test_row_staged_D_in_mixed_cg(variant):
-    # the mixed-precision CG's D pass with a row-staged tile (its |D p|^2 CTA
-    # partials are summed over the steps of a ring CTA): the solve reaches an
-    # oracle-recomputed residual <= 1e-10 in the iterations of the default tile
+@pytest.mark.parametrize("op, variant, sgrp",
+                         [(dw.DW_OP_D, 6, 2), (dw.DW_OP_D, 7, 2), (dw.DW_OP_DDAG, 4, 2),
+                          (dw.DW_OP_DDAG, 5, 4)],
+                         ids=["D_v6", "D_v7", "Ddag_cluster2", "Ddag_cluster4"])
+def test_forced_tiles_in_mixed_cg(op, variant, sgrp):
+    # the mixed-precision CG with the D pass in a row-staged tile (its |D p|^2
+    # CTA partials are summed over the steps of a ring CTA), or the D^+ pass
+    # (which applies the residual update itself) in a tile whose slice groups
+    # form a thread-block cluster: the solve reaches an oracle-recomputed
+    # residual <= 1e-10 in the iterations of the default tiles
     dims, Ls, nrhs = (32, 4, 4, 4), 8, 2
     U, eta = make_case(dims, Ls, nrhs, seed=23)
     mfs = [0.1, 0.3]
@@ -187,7 +194,8 @@ def test_row_staged_D_in_mixed_cg(variant):
         lat = _lattice(dims, Ls, dw.DW_MOBIUS, dw.DW_F64)
         lat.load_gauge(U)
         if forced:
-            lat.set_tile(dw.DW_OP_D, 2, 64, variant, nrhs=nrhs, prec=dw.DW_F32, sgrp=2)
+            lat.set_tile(op, 2 if op == dw.DW_OP_D else 1, 64, variant, nrhs=nrhs,
+                         prec=dw.DW_F32, sgrp=sgrp)
         b = lat.pack(eta)
         x = lat.empty(nrhs)
         x.zero_()
@@ -407,7 +415,7 @@ def test_tune_picks_valid_tile_and_stays_exact():
         spt, tx, variant, zblk, sgrp = lat.tune(op, 1)
         assert dims[2] % zblk == 0
         assert Ls % spt == 0 and tx % 32 == 0 and tx * (Ls // spt) <= 1024
-        assert (Ls // spt) % sgrp == 0 and (sgrp == 1 or op != dw.DW_OP_DDAG)
+        assert (Ls // spt) % sgrp == 0 and (sgrp <= 8 or op != dw.DW_OP_DDAG)
         assert variant in range(8)
         got = run_gpu(lat, op, psi, mf=[0.01])
         ref = run_oracle(op, psi, U, dims, Ls, 1.8, 1.5, 0.5, [0.01])
@@ -462,9 +470,14 @@ def test_argument_errors():
     with pytest.raises(dw.DWError) as e:
         lat.set_tile(dw.DW_OP_DHOP, 1, 32, sgrp=3)  # 3 does not divide Ls / spt = 4
     assert e.value.code == dw.DW_ERR_ARG
-    with pytest.raises(dw.DWError) as e:
-        lat.set_tile(dw.DW_OP_DDAG, 1, 32, sgrp=2)  # D^+ keeps all slices in one CTA
-    assert e.value.code == dw.DW_ERR_ARG
     assert "multiple" in dw.dw_last_error() or "invalid" in dw.dw_last_error()
     torch.cuda.synchronize()
     lat.close()
+    # D^+ spreads a tile's slice groups over a thread-block cluster of sgrp CTAs:
+    # at most the portable cluster size, 8
+    lat16 = _lattice(dims, 16, dw.DW_MOBIUS, dw.DW_F32)
+    lat16.set_tile(dw.DW_OP_DDAG, 1, 32, sgrp=8)
+    with pytest.raises(dw.DWError) as e:
+        lat16.set_tile(dw.DW_OP_DDAG, 1, 32, sgrp=16)
+    assert e.value.code == dw.DW_ERR_ARG
+    lat16.close()
