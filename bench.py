@@ -535,6 +535,9 @@ def main():
                     help="operator timed with --main-only (profiling runs; --tile applies "
                          "to it): the hopping term, D or D^+ at mass m_f")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--solvers-only", action="store_true",
+                    help="run only the CG and even-odd solver legs (profiling runs); "
+                         "prints their JSON")
     ap.add_argument("--cg-full", action="store_true",
                     help="also run the three CGs on the benchmark lattice (minutes)")
     args = ap.parse_args()
@@ -559,6 +562,11 @@ def main():
     from paper_2112_01852_gb300 import dw, inputs
     from paper_2112_01852_gb300.lattice import Lattice
     cuda_build.build()
+    if args.solvers_only:
+        out = {"cg": bench_cg(args), "cg_eo": bench_eo(args)}
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return 0
 
     if not args.main_only and (args.prec != "f32" or args.nrhs != 1 or args.op != "dhop"):
         ap.error("--prec, --nrhs and --op apply to --main-only runs")

@@ -188,9 +188,33 @@ class DistLattice:
                           list(b), nrhs, st)
 
     def cg(self, x, b, mf, nrhs=1, tol=1e-10, maxit=10000):
-        """D^+D x = b on the decomposed lattice (FP64 CG); x holds the start vector.
-        Returns (converged[nrhs], iterations, true residual[nrhs])."""
+        """D^+D x = b on the decomposed lattice (CG at this lattice's precision); x
+        holds the start vector.  Returns (converged[nrhs], iterations, true
+        residual[nrhs])."""
         return cg(_LatticeOps(self, mf, nrhs), x, b, nrhs, tol, maxit)
+
+    def convert(self, other, out, inp, nrhs=1):
+        """out (a field of DistLattice `other`: the same sub-lattice at another
+        precision) = inp (a field of this one), through the canonical complex128
+        layout on the device (dw_unpack_fermion, then dw_pack_fermion)."""
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+        V5 = self.Vf * self.Lt_loc * self.Ls
+        buf = torch.empty(nrhs * V5 * 24, dtype=torch.float64, device="cuda")
+        dw.dw_unpack_fermion(self.lat.handle, buf.data_ptr(), inp.data_ptr(), self.prec, nrhs,
+                             st)
+        dw.dw_pack_fermion(other.lat.handle, out.data_ptr(), other.prec, buf.data_ptr(), nrhs,
+                           st)
+
+    def cg_mixed(self, lo, x, b, mf, nrhs=1, tol=1e-10, maxit=10000, inner_tol=1e-5):
+        """D^+D x = b with this (high-precision) lattice for the residuals and the
+        solution and DistLattice `lo` (same sub-lattice, lower precision) for the
+        inner solves: defect correction, see mixed_cg.  Returns (converged[nrhs],
+        inner iterations, outer steps, true residual[nrhs])."""
+        hi_ops, lo_ops = _LatticeOps(self, mf, nrhs), _LatticeOps(lo, mf, nrhs)
+        return mixed_cg(hi_ops, lo_ops, lambda o, i: self.convert(lo, o, i, nrhs),
+                        lambda o, i: lo.convert(self, o, i, nrhs), x, b, nrhs, tol, maxit,
+                        inner_tol)
 
     def close(self):
         self._halo.clear()
@@ -257,3 +281,40 @@ def cg(ops, x, b, nrhs, tol, maxit, restarts=3):
             iters += 1
     converged = [t <= tol for t in true_res]
     return converged, iters, true_res
+
+
+def mixed_cg(hi, lo, to_lo, to_hi, x, b, nrhs, tol, maxit, inner_tol=1e-5, max_outer=30):
+    """Mixed-precision solve of A x = b by defect correction (iterative
+    refinement; Wilkinson's scheme, as used for mixed-precision solvers): the
+    residual r = b - A x and the solution x stay at the high precision of vector
+    space ``hi``; each outer step converts r to the low-precision space ``lo``,
+    solves A e = r there with CG (above) to the relative tolerance ``inner_tol``
+    and adds the correction e back to x at high precision.  It stops when every
+    RHS's high-precision true residual |b - A x| / |b| meets tol (an RHS that
+    already meets it gets a zero correction), after ``maxit`` inner iterations
+    or after ``max_outer`` outer steps.  ``to_lo(out_lo, in_hi)`` and
+    ``to_hi(out_hi, in_lo)`` convert a vector.  Returns (converged, inner
+    iterations, outer steps, true_resid)."""
+    r, Ax, e_hi = hi.new(), hi.new(), hi.new()
+    r_lo, e_lo = lo.new(), lo.new()
+    bb = hi.dot(b, b)
+    iters = outer = 0
+    while True:
+        hi.apply(Ax, x)                                  # r = b - A x
+        hi.axpby(r, [1.0] * nrhs, b, [0.0] * nrhs)
+        hi.axpby(r, [-1.0] * nrhs, Ax, [1.0] * nrhs)
+        rr = hi.dot(r, r)
+        true_res = [np.sqrt(v / w) if w > 0 else 0.0 for v, w in zip(rr, bb)]
+        done = [t <= tol for t in true_res]
+        if all(done) or iters >= maxit or outer >= max_outer:
+            break
+        # the converged RHS solve A e = 0: their correction is zero
+        hi.axpby(r, [0.0 if d else 1.0 for d in done], r, [0.0] * nrhs)
+        to_lo(r_lo, r)
+        lo.axpby(e_lo, [0.0] * nrhs, r_lo, [0.0] * nrhs)  # e = 0
+        _, n, _ = cg(lo, e_lo, r_lo, nrhs, inner_tol, maxit - iters, restarts=0)
+        iters += n
+        outer += 1
+        to_hi(e_hi, e_lo)
+        hi.axpby(x, [1.0] * nrhs, e_hi, [1.0] * nrhs)
+    return done, iters, outer, true_res

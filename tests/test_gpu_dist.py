@@ -7,7 +7,9 @@ launches.
 * The stitched Dhop, Dhop^+, D and D^+ equal the undecomposed kernels (same
   variant-0 tiles) bit for bit, at FP64 and FP32, and match the oracle.
 * The distributed FP64 CG on D^+D (global sums over both ranks) reaches an
-  oracle-recomputed residual <= 1e-10.
+  oracle-recomputed residual <= 1e-10, and so does the distributed mixed-
+  precision solve (FP64 residuals and solution, FP32 inner CG on a second
+  decomposed lattice, by defect correction).
 """
 
 import socket
@@ -61,6 +63,22 @@ def _worker(rank, world, port, path):
             res["cg_iters"] = np.array(iters)
             res["cg_res"] = np.array(true_res)
         dl.close()
+    hi = dist.DistLattice(comm, DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64,
+                          bc=BC)
+    lo = dist.DistLattice(comm, DIMS, LS, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F32,
+                          bc=BC)
+    hi.load_gauge(U)
+    lo.load_gauge(U)
+    xb = hi.pack(psi)
+    xm = hi.empty(2)
+    xm.zero_()
+    conv, iters, outer, true_res = hi.cg_mixed(lo, xm, xb, MF, 2, tol=1e-10, maxit=8000)
+    res["mcg_x"] = hi.gather(xm, 2)
+    res["mcg_conv"] = np.array(conv)
+    res["mcg_outer"] = np.array(outer)
+    res["mcg_res"] = np.array(true_res)
+    hi.close()
+    lo.close()
     if rank == 0:
         np.savez(path, **res)
     tdist.barrier()
@@ -117,3 +135,14 @@ def test_two_process_cg(two_ranks):
         rel = np.linalg.norm((psi[r] - Ax[r]).ravel()) / np.linalg.norm(psi[r].ravel())
         assert rel <= 1e-10, (r, rel)
         assert abs(two_ranks["cg_res"][r] - rel) <= 1e-3 * rel + 1e-15
+
+
+def test_two_process_mixed_cg(two_ranks):
+    U, psi = make_case(DIMS, LS, 2, seed=71, links="haar")
+    x = two_ranks["mcg_x"]
+    assert two_ranks["mcg_conv"].all() and 2 <= int(two_ranks["mcg_outer"]) <= 10
+    Ax = oracle.dwdagdw(x, U, DIMS, LS, M5, B, C, MF, BC)
+    for r in range(2):
+        rel = np.linalg.norm((psi[r] - Ax[r]).ravel()) / np.linalg.norm(psi[r].ravel())
+        assert rel <= 1e-10, (r, rel)
+        assert abs(two_ranks["mcg_res"][r] - rel) <= 1e-3 * rel + 1e-15

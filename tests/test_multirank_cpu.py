@@ -53,12 +53,13 @@ def test_two_ranks_gloo_max_time_and_total_rate():
 # the dense solution.
 
 
-def _ring_ops(comm, n_loc, nrhs, m2):
+def _ring_ops(comm, n_loc, nrhs, m2, dtype=None):
     import torch
+    dtype = torch.float64 if dtype is None else dtype
 
     class RingOps:
         def new(self):
-            return torch.zeros(nrhs, n_loc, dtype=torch.float64)
+            return torch.zeros(nrhs, n_loc, dtype=dtype)
 
         def apply(self, out, inp):
             # faces: the first site goes to the rank below, the last to the rank above
@@ -74,7 +75,8 @@ def _ring_ops(comm, n_loc, nrhs, m2):
             return comm.allreduce((a * b).sum(dim=1).tolist())
 
         def axpby(self, y, a, x, b):
-            y.copy_(torch.tensor(a)[:, None] * x + torch.tensor(b)[:, None] * y)
+            y.copy_(torch.tensor(a, dtype=dtype)[:, None] * x +
+                    torch.tensor(b, dtype=dtype)[:, None] * y)
 
     return RingOps()
 
@@ -105,7 +107,17 @@ def _dist_worker(rank, world, port, out):
     x = ops.new()
     conv, iters, res = dist.cg(ops, x, b, nrhs, 1e-12, 500)
     xs = comm.allgather_numpy(x.numpy())
-    out[rank] = (exch, red, conv, iters, res, np.concatenate(xs, axis=1) if world > 1 else xs)
+    # mixed precision by defect correction: float64 residuals and solution,
+    # float32 inner CG
+    lo = _ring_ops(comm, n_loc, nrhs, m2, torch.float32)
+    xm = ops.new()
+    mconv, miters, mouter, mres = dist.mixed_cg(ops, lo, lambda o, i: o.copy_(i),
+                                                lambda o, i: o.copy_(i), xm, b, nrhs, 1e-12,
+                                                2000, inner_tol=1e-4)
+    xms = comm.allgather_numpy(xm.numpy())
+    out[rank] = (exch, red, conv, iters, res, np.concatenate(xs, axis=1) if world > 1 else xs,
+                 (mconv, miters, mouter, mres,
+                  np.concatenate(xms, axis=1) if world > 1 else xms))
     tdist.destroy_process_group()
 
 
@@ -123,7 +135,10 @@ def test_gloo_data_plane_and_distributed_cg(world):
     bglob = np.random.default_rng(7).standard_normal((nrhs, N))
     want = np.linalg.solve(A, bglob.T).T
     for rank in range(world):
-        exch, red, conv, iters, res, x = out[rank]
+        exch, red, conv, iters, res, x, mixed = out[rank]
+        mconv, miters, mouter, mres, xm = mixed
+        assert all(mconv) and max(mres) <= 1e-12 and 2 <= mouter <= 8, (mouter, mres)
+        assert np.allclose(xm, want, rtol=0, atol=1e-10)
         up, dn = (rank + 1) % world, (rank - 1) % world
         # recv_up is the rank above's send_dn, recv_dn the rank below's send_up
         assert exch == (10.0 * up + 1.0, 10.0 * dn + 2.0)
