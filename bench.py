@@ -564,6 +564,9 @@ def main():
     cuda_build.build()
     if args.solvers_only:
         out = {"cg": bench_cg(args), "cg_eo": bench_eo(args)}
+        if args.cg_full:
+            out["cg_full"] = bench_cg(args, DIMS, LS, SEED)
+            out["cg_eo_full"] = bench_eo(args, DIMS, LS, SEED, f64=False)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return 0

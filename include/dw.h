@@ -338,6 +338,21 @@ int dw_set_complex_layout(dw_lattice *lat, int interleaved);
 int dw_set_wait_polls(dw_lattice *lat, int polls);
 
 /*
+ * Reliable-update threshold of the mixed-precision solvers (dw_cg_solve and
+ * dw_solve_eo with mode DW_F32 or DW_F16) on this lattice: the FP64 residual is
+ * recomputed (and the low-precision iteration restarted from it) once the
+ * iterated residual has fallen below delta times its largest value since the
+ * previous update (Clark et al., mixed-precision solvers on GPUs; the paper
+ * gives no solver).  0 < delta < 1 sets it; delta = 0 (the default) takes the
+ * values measured fastest at 24^4 x Ls=16: for dw_cg_solve 1e-3 with FP32 and
+ * 0.1 with FP16 inner fields, for dw_solve_eo 1e-4 and 0.01.  Smaller values
+ * mean fewer FP64 operator applications, larger ones a shorter drift of the
+ * iterated residual.
+ * Returns DW_OK or DW_ERR_ARG (delta outside [0, 1)).
+ */
+int dw_set_reliable_delta(dw_lattice *lat, double delta);
+
+/*
  * Domain decomposition along t on one device ("virtual ranks").  The hopping
  * term has one exchange step when the lattice is split into ranks along t
  * (an exchange of spin-projected half spinors across the cut).  A rank owns a

@@ -299,6 +299,7 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
   lat->prec = prec;
   lat->wait_polls = -1;
   lat->cplx = false;
+  lat->reliable_delta = 0.0;
   cudaGetDevice(&lat->device);
   cudaDeviceGetAttribute(&lat->num_sms, cudaDevAttrMultiProcessorCount, lat->device);
   for (int p = 0; p < 3; ++p) {
@@ -467,6 +468,15 @@ int dw_set_wait_polls(dw_lattice *lat, int polls) {
   if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
   if (polls < -1) return fail(DW_ERR_ARG, "polls must be >= -1 (got %d)", polls);
   lat->wait_polls = polls;
+  return DW_OK;
+}
+
+int dw_set_reliable_delta(dw_lattice *lat, double delta) {
+  clear_error();
+  if (!lat) return fail(DW_ERR_ARG, "lattice is NULL");
+  if (!(delta >= 0.0 && delta < 1.0))
+    return fail(DW_ERR_ARG, "the reliable-update threshold must be in [0, 1) (got %g)", delta);
+  lat->reliable_delta = delta;
   return DW_OK;
 }
 

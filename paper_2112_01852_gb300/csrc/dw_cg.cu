@@ -179,10 +179,16 @@ int cg_run(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs, 
            std::chrono::steady_clock::time_point t_start) {
   CGWork *w = lat->cg;
   cudaError_t e;
-  // reliable-update threshold: 0.01 with FP32 inner fields, 0.1 with FP16
-  // ones (their rounding, 2^-11, would make the iterated residual drift too far
-  // over a longer stretch); both reach the same iteration counts
-  const double delta = mode == DW_F64 ? 0.0 : (mode == DW_F32 ? 0.01 : 0.1);
+  // reliable-update threshold (dw_set_reliable_delta), by default the fastest
+  // measured at 24^4 x 16 (every setting reaches the same residual): CG on D^+D
+  // 1e-3 with FP32 inner fields, 0.1 with FP16 ones (their rounding, 2^-11,
+  // makes the iterated residual drift further between updates); the even-odd
+  // solve, whose inner iterations are cheaper against its FP64 updates, 1e-4
+  // (FP32) and 0.01 (FP16)
+  const double delta = mode == DW_F64                 ? 0.0
+                       : lat->reliable_delta > 0.0 ? lat->reliable_delta
+                       : eo ? (mode == DW_F32 ? 1e-4 : 0.01)
+                            : (mode == DW_F32 ? 1e-3 : 0.1);
   Solve S{lat, w, nrhs, mode, mode == DW_F64 ? DW_F64 : DW_F32, delta,
           tol, maxit, mf, w->stream,
           BlasCtx((int)(eo ? lat->V4 / 2 : lat->V4), lat->Ls, nrhs, lat->num_sms), eo};

@@ -282,6 +282,7 @@ struct dw_lattice {
   int *dev_status;  // device word the kernels set when a bounded wait gives up
   int wait_polls;   // dw_set_wait_polls (-1: the kernels' built-in bound)
   bool cplx;        // dw_set_complex_layout: FP32 fields hold interleaved-complex quads
+  double reliable_delta;  // dw_set_reliable_delta (0: 0.01 FP32 / 0.1 FP16 inner fields)
   // gauge copies per precision (blocked; 18 reals per link at FP64, 12 below)
   void *gauge[3];
   // scratch: one field for D^+D, host-apply staging, reduction partials

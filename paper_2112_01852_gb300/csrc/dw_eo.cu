@@ -388,7 +388,7 @@ int tune_cb(dw_lattice *lat, int prec, int op, cudaStream_t st) {
   float best = 1e30f;
   const int za = auto_zblk(lat, prec);
   for (int spt : {1, 2, 3, 4})
-    for (int tx : {32, 64, 128})
+    for (int tx : {32, 64, 96, 128})
       for (int sgrp : {1, 2, 3, 4, 6}) {
         if (lat->Ls % spt || (lat->Ls / spt) % sgrp || (op == OP_DDAG && sgrp > 8)) continue;
         const TileConfig t{spt, tx, prec == DW_F64 ? 0 : 4, za, sgrp};

@@ -33,7 +33,7 @@ int tune_tile(dw_lattice *lat, int prec, int op, int nrhs, cudaStream_t st, bool
   }
   for (int variant = 0; variant < kNumVariants; ++variant)
     for (int spt : {1, 2, 3, 4})
-      for (int tx : {32, 64, 128, 256})
+      for (int tx : {32, 64, 96, 128, 192, 256})  // 96, 192: planes of 24 x 24 sites
         for (int zblk : zbs)
           for (int sgrp : {1, 2, 3, 4, 6})
           for (int outer = 0; outer < (nrhs > 1 ? 2 : 1); ++outer) {

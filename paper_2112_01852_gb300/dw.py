@@ -57,7 +57,7 @@ SYMBOLS = (
     "dw_unpack_fermion", "dw_last_error", "dw_fermion_bytes_eo", "dw_eo_split", "dw_eo_merge",
     "dw_apply_m5_eo", "dw_apply_schur", "dw_solve_eo", "dw_get_tile", "dw_set_wait_polls",
     "dw_set_complex_layout", "dw_halo_pack_op", "dw_apply_op_halo", "dw_field_redot",
-    "dw_field_axpby",
+    "dw_field_axpby", "dw_set_reliable_delta",
 )
 
 
@@ -112,6 +112,7 @@ def load_library():
             "dw_get_tile": (I, [P, I, I, I, IP, IP, IP, IP, IP]),
             "dw_device_status": (I, [P]),
             "dw_set_wait_polls": (I, [P, I]),
+            "dw_set_reliable_delta": (I, [P, D]),
             "dw_set_complex_layout": (I, [P, I]),
             "dw_fermion_bytes_eo": (S, [P, I, I]),
             "dw_eo_split": (I, [P, P, P, P, I, I, P]),
@@ -251,6 +252,10 @@ def dw_set_complex_layout(lat, interleaved):
 
 def dw_set_wait_polls(lat, polls):
     _check(load_library().dw_set_wait_polls(lat, int(polls)))
+
+
+def dw_set_reliable_delta(lat, delta):
+    _check(load_library().dw_set_reliable_delta(lat, float(delta)))
 
 
 def dw_fermion_bytes_eo(lat, prec, nrhs):

@@ -173,3 +173,30 @@ def test_cg_tunes_its_inner_operator():
         assert Ls % spt == 0 and tx % 32 == 0 and dims[2] % zblk == 0
         assert (Ls // spt) % sgrp == 0 and (op == dw.DW_OP_D or sgrp <= 8)
     lat.close()
+
+
+def test_reliable_delta_setting():
+    # dw_set_reliable_delta: values outside [0, 1) are refused; a smaller
+    # threshold means fewer FP64 reliable updates, and every setting still
+    # reaches an oracle-recomputed residual <= 1e-10
+    from paper_2112_01852_gb300.lattice import Lattice
+    dims, Ls = (8, 8, 8, 8), 8
+    U, rhs = make_case(dims, Ls, 1, seed=22)
+    lat = Lattice(dims, Ls, kind=dw.DW_MOBIUS, M5=M5, b=B, c=C, prec=dw.DW_F64)
+    lat.load_gauge(U)
+    for bad in (-0.1, 1.0, float("nan")):
+        with pytest.raises(dw.DWError) as e:
+            dw.dw_set_reliable_delta(lat.handle, bad)
+        assert e.value.code == dw.DW_ERR_ARG
+    b = lat.pack(rhs)
+    updates = {}
+    for delta in (0.1, 1e-5, 0.0):  # 0: the default, 1e-3 for FP32 inner fields
+        dw.dw_set_reliable_delta(lat.handle, delta)
+        x = lat.empty(1)
+        x.zero_()
+        status, stats = lat.cg(x, b, [0.01], nrhs=1, tol=1e-10, maxit=20000, mode=dw.DW_F32)
+        assert status == dw.DW_OK and stats[0].converged == 1
+        assert _true_resid(lat.unpack(x, 1), rhs, U, dims, Ls, [0.01])[0] <= 1e-10
+        updates[delta] = stats[0].reliable_updates
+    assert updates[1e-5] <= updates[0.0] < updates[0.1], updates
+    lat.close()
