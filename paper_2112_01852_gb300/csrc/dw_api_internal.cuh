@@ -1,8 +1,53 @@
 // Internal helpers shared by the C-ABI translation units.
 #pragma once
 
+#include <map>
+#include <tuple>
+#include <vector>
+
 #include "dw_common.cuh"
 #include "dw_fields.cuh"
+
+namespace dw {
+struct CGWork;
+}  // namespace dw
+
+// ---------------------------------------------------------------------------
+// The lattice object behind the opaque handle.
+struct dw_lattice {
+  int dims[4];
+  int Ls;
+  long long V4;
+  long long V4p;  // V4 padded to a multiple of 32 (blocked layout)
+  long long V5;
+  int kind;
+  double M5, b, c;
+  int prec;
+  int bc[4];
+  int device;
+  int num_sms;
+  bool gauge_loaded;
+  int *dev_status;  // device word the kernels set when a bounded wait gives up
+  int wait_polls;   // dw_set_wait_polls (-1: the kernels' built-in bound)
+  bool cplx;        // dw_set_complex_layout: FP32 fields hold interleaved-complex quads
+  double reliable_delta;  // dw_set_reliable_delta (0: the solvers' defaults)
+  // gauge copies per precision (blocked; 18 reals per link at FP64, 12 below)
+  void *gauge[3];
+  // scratch: one field for D^+D, host-apply staging, reduction partials
+  void *scratch;
+  size_t scratch_bytes;
+  void *stage_in, *stage_out;
+  size_t stage_bytes;
+  // host-buffer apply: copy-in and copy-out streams and their events
+  cudaStream_t pipe_in, pipe_out;
+  std::vector<cudaEvent_t> pipe_events;
+  double *partials;   // reduction partials
+  size_t partials_cap;
+  // tuning cache: (prec, op, nrhs) -> tile
+  std::map<std::tuple<int, int, int>, dw::TileConfig> tuned;
+  // solver workspace (dw_cg_solve), created on first use
+  dw::CGWork *cg;
+};
 
 namespace dw {
 

@@ -1,5 +1,6 @@
 // Common definitions of the GB300 domain-wall library: precision traits, vector
-// load/convert helpers, kernel parameter blocks and the lattice object.
+// load/convert helpers and the kernel parameter blocks (the lattice object is
+// host-side only: dw_api_internal.cuh).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -7,10 +8,7 @@
 
 #include <cstddef>
 #include <cstdint>
-#include <map>
-#include <vector>
 #include <string>
-#include <tuple>
 
 #include "dw.h"
 
@@ -260,43 +258,6 @@ int launch_halo_pack_F32(const DslashParams &p, void *send_dn, void *send_up, in
 int launch_halo_pack_F16(const DslashParams &p, void *send_dn, void *send_up, int op,
                          cudaStream_t st);
 
-struct CGWork;
-
 }  // namespace dw
 
-// ---------------------------------------------------------------------------
-// The lattice object behind the opaque handle.
-struct dw_lattice {
-  int dims[4];
-  int Ls;
-  long long V4;
-  long long V4p;  // V4 padded to a multiple of 32 (blocked layout)
-  long long V5;
-  int kind;
-  double M5, b, c;
-  int prec;
-  int bc[4];
-  int device;
-  int num_sms;
-  bool gauge_loaded;
-  int *dev_status;  // device word the kernels set when a bounded wait gives up
-  int wait_polls;   // dw_set_wait_polls (-1: the kernels' built-in bound)
-  bool cplx;        // dw_set_complex_layout: FP32 fields hold interleaved-complex quads
-  double reliable_delta;  // dw_set_reliable_delta (0: 0.01 FP32 / 0.1 FP16 inner fields)
-  // gauge copies per precision (blocked; 18 reals per link at FP64, 12 below)
-  void *gauge[3];
-  // scratch: one field for D^+D, host-apply staging, reduction partials
-  void *scratch;
-  size_t scratch_bytes;
-  void *stage_in, *stage_out;
-  size_t stage_bytes;
-  // host-buffer apply: copy-in and copy-out streams and their events
-  cudaStream_t pipe_in, pipe_out;
-  std::vector<cudaEvent_t> pipe_events;
-  double *partials;   // reduction partials
-  size_t partials_cap;
-  // tuning cache: (prec, op, nrhs) -> tile
-  std::map<std::tuple<int, int, int>, dw::TileConfig> tuned;
-  // solver workspace (dw_cg_solve), created on first use
-  dw::CGWork *cg;
-};
+
