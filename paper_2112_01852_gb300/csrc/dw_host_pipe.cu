@@ -46,7 +46,7 @@ int pipe_events(dw_lattice *lat, size_t n) {
 // Number of slabs: the largest divisor of Lt that is at most kMaxSlabs and
 // leaves slabs of at least kMinSlabSites 4D sites (smaller launches do not
 // fill the GPU).
-constexpr int kMaxSlabs = 16;
+constexpr int kMaxSlabs = 64;
 constexpr long long kMinSlabSites = 8192;
 
 int slab_count(const dw_lattice *lat) {

@@ -384,11 +384,13 @@ def test_apply_host_matches_device():
     lat.close()
 
 
-@pytest.mark.parametrize("dims", [(16, 16, 8, 16), (32, 16, 16, 16), (16, 16, 16, 6)],
-                         ids=["4slabs", "16slabs_T1", "3slabs"])
+@pytest.mark.parametrize("dims", [(16, 16, 8, 16), (32, 16, 16, 16), (16, 16, 16, 6),
+                                  (32, 16, 16, 40)],
+                         ids=["4slabs", "16slabs_T1", "3slabs", "40slabs_T1"])
 def test_apply_host_slab_pipeline_matches_device(dims):
     # Lx Ly Lz a multiple of 32: the host apply moves the field in t slabs
-    # (4, 16 of one time slice, 3) and must equal the device apply bit for bit
+    # (4, 16 of one time slice, 3, 40 of one slice) and must equal the device
+    # apply bit for bit
     import torch
     Ls = 4
     U, psi = make_case(dims, Ls, 2, seed=14)
