@@ -189,6 +189,10 @@ int run_dslash(dw_lattice *lat, int prec, int op, void *out, const void *in,
       p.rs_alpha = fuse->alpha + (size_t)r0 * fuse->alpha_stride;
       p.rs_alpha_stride = fuse->alpha_stride;
       p.rs_partials = fuse->partials + (size_t)r0 * dslash_ctas_per_rhs(lat, cfg);
+      if (fuse->x_s && fuse->p) {
+        p.xs = (char *)fuse->x_s + (size_t)r0 * rs_rhs_bytes;
+        p.pdir = (const char *)fuse->p + (size_t)r0 * rhs_bytes;
+      }
     }
     int rc;
     if (lat->cplx && prec == DW_F32) {

@@ -231,15 +231,17 @@ __global__ void __launch_bounds__(kBlasThreads)
 
 // x_s += alpha p for every RHS whose step computed alpha (including those that
 // now wait for a reliable update), then p = r_s + beta p for those that go on
-// iterating: one read of p serves both.
+// iterating: one read of p serves both.  update_x = false: the D^+ pass made the
+// x_s step already, only the direction is left.
 template <class PP, class PR>
 __global__ void __launch_bounds__(kBlasThreads)
     cg_direction_kernel(void *p, void *x_s, const void *r_s, SlotGeom L, size_t bpp,
-                        size_t bpr, const CGState *st) {
+                        size_t bpr, const CGState *st, bool update_x) {
   const int rhs = blockIdx.y;
   const CGState &S = st[rhs];
   if (!S.xpend) return;
   const bool next = S.run != 0;
+  if (!update_x && !next) return;
   using A = typename Arith<PP, PR>::T;
   const A a = (A)S.alpha;
   const A b = (A)S.beta;
@@ -249,12 +251,15 @@ __global__ void __launch_bounds__(kBlasThreads)
   SLOT_LOOP(i) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      A pv[4], xv[4];
+      A pv[4];
       ld4<PP>(pv, pp, q, i);
-      ld4<PR>(xv, pxs, q, i);
+      if (update_x) {
+        A xv[4];
+        ld4<PR>(xv, pxs, q, i);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) xv[k] += a * pv[k];
-      st4<PR>(pxs, q, i, xv);
+        for (int k = 0; k < 4; ++k) xv[k] += a * pv[k];
+        st4<PR>(pxs, q, i, xv);
+      }
       if (next) {
         A rv[4];
         ld4<PR>(rv, prs, q, i);
@@ -495,11 +500,11 @@ int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r
 }
 
 int cg_direction(const BlasCtx &c, int pp, int pr, void *p, void *x_s, const void *r_s,
-                 const CGState *st, cudaStream_t s) {
+                 const CGState *st, cudaStream_t s, bool update_x) {
   dim3 grid(c.nblk, c.nrhs);
   DISPATCH_PREC(pp, PP, DISPATCH_PREC(pr, PR,
       cg_direction_kernel<PP, PR><<<grid, kBlasThreads, 0, s>>>(
-          p, x_s, r_s, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), st)));
+          p, x_s, r_s, c.geom, rbytes(pp, c.geom), rbytes(pr, c.geom), st, update_x)));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

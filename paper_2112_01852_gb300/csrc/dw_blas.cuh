@@ -64,10 +64,11 @@ int cg_accumulate_x(const BlasCtx &c, int pr, void *x, const void *x_s, const CG
                     cudaStream_t s);
 int cg_reliable_apply(const BlasCtx &c, int pp, int pr, const double *r, void *r_s, void *x_s,
                       void *p, const CGState *st, cudaStream_t s);
-// x_s += alpha p and p = r_s + beta p with one read of p (the r_s -= alpha Ap
+// x_s += alpha p (unless update_x is false: the D^+ pass made that step, see
+// DslashParams::xs) and p = r_s + beta p with one read of p (the r_s -= alpha Ap
 // of the step is fused into the D^+ pass, see DslashParams::rs).
 int cg_direction(const BlasCtx &c, int pp, int pr, void *p, void *x_s, const void *r_s,
-                 const CGState *st, cudaStream_t s);
+                 const CGState *st, cudaStream_t s, bool update_x = true);
 // alpha = rr / <p, Ap> with <p, Ap> summed from nblk partials per RHS.
 int cg_alpha(const BlasCtx &c, const double *partial, int nblk, CGState *st, cudaStream_t s);
 // nblk: partials per RHS (-1: c.nblk, the BLAS grid; a fused D^+ pass leaves one

@@ -114,8 +114,10 @@ struct Solve {
     if (rc) return rc;
     if (cg_alpha(c, w->dnorm, nd, w->state, st))
       return cuda_fail(cudaGetLastError(), "cg iteration launch");
+    // ... and the solution step x_s += alpha p, which leaves the direction pass
+    // three field accesses instead of five
     const ResidualFuse fuse{w->rs, &w->state[0].alpha, (int)(sizeof(CGState) / sizeof(double)),
-                            w->rsnorm};
+                            w->rsnorm, w->xs, w->p};
     if (eo)
       rc = apply_schur(lat, pp, w->Ap, w->tmp, mf, nrhs, true, w->e1, w->e2, st, gate_run(),
                        kCGStateInts, nullptr, &fuse);
@@ -125,7 +127,7 @@ struct Solve {
     if (rc) return rc;
     if (cg_beta(c, w->rsnorm, w->state, delta, tol, maxit, st, ctas_ddag()))
       return cuda_fail(cudaGetLastError(), "cg iteration launch");
-    if (cg_direction(c, pp, pr, w->p, w->xs, w->rs, w->state, st))
+    if (cg_direction(c, pp, pr, w->p, w->xs, w->rs, w->state, st, false))
       return cuda_fail(cudaGetLastError(), "cg iteration launch");
     return DW_OK;
   }

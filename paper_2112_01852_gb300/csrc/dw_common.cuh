@@ -184,14 +184,21 @@ struct DslashParams {
   const double *rs_alpha;  // alpha of RHS r at rs_alpha[r * rs_alpha_stride]
   int rs_alpha_stride;
   double *rs_partials;
+  // optional with rs: also the solution step x_s += alpha_rhs p of the same
+  // iteration (x_s like r_s, p the CG direction at the operator's precision)
+  void *xs;
+  const void *pdir;
 };
 
-// The residual update fused into a D^+ launch (see DslashParams::rs).
+// The residual update fused into a D^+ launch (see DslashParams::rs), and
+// optionally the solution step (x_s and p non-null; see DslashParams::xs).
 struct ResidualFuse {
   void *r_s;
   const double *alpha;
   int alpha_stride;
   double *partials;
+  void *x_s = nullptr;
+  const void *p = nullptr;
 };
 
 constexpr int kMaxRhsPerLaunch = 64;

@@ -1543,6 +1543,8 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
     using rvec = typename PR::vec;
     constexpr int RNPV = 24 / PR::R;
     constexpr int RVPQ = 4 / PR::R;
+    constexpr int PNPV = 24 / P::R;  // the direction p, at the operator's precision
+    constexpr int PVPQ = 4 / P::R;
     double rsq = 0.0;
     if (active) {
       const int gn = (chunk + 1 == tch) ? 0 : chunk + 1;  // neighbouring chunks of the tile
@@ -1602,6 +1604,23 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
             }
           }
           rsq += (double)ss;
+          if (p.xs) {
+            // the solution step of the same iteration, x_s += alpha p
+            const V2 pa = bc<V2>((C)p.rs_alpha[(long long)rhs * p.rs_alpha_stride]);
+            rvec *xb = reinterpret_cast<rvec *>(p.xs) + (long long)rhs * p.rs_stride +
+                       site_off(xf, s0 + j, Ls, RNPV);
+            const vec *pb = reinterpret_cast<const vec *>(p.pdir) +
+                            (long long)rhs * p.rhs_stride + site_off(xf, s0 + j, Ls, PNPV);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              V2 pr_, pi_, xr, xi;
+              quad_in(pr_, pi_, pb + (long long)q * PVPQ * kPlaneStride, kPlaneStride);
+              quad_in(xr, xi, xb + (long long)q * RVPQ * kPlaneStride, kPlaneStride);
+              xr = p_fma(pa, pr_, xr);
+              xi = p_fma(pa, pi_, xi);
+              quad_out(xb + (long long)q * RVPQ * kPlaneStride, kPlaneStride, xr, xi);
+            }
+          }
         } else {
           store(j, o);
         }

@@ -334,6 +334,10 @@ int run_dslash_cb(dw_lattice *lat, int prec, int op, void *out, const void *nbr,
       p.rs_alpha = fuse->alpha + (size_t)r0 * fuse->alpha_stride;
       p.rs_alpha_stride = fuse->alpha_stride;
       p.rs_partials = fuse->partials + (size_t)r0 * ctas;
+      if (fuse->x_s && fuse->p) {
+        p.xs = (char *)fuse->x_s + (size_t)r0 * rs_rhs_bytes;
+        p.pdir = (const char *)fuse->p + (size_t)r0 * rhs_bytes;
+      }
     }
     const int rc = launch_dslash_cb(p, prec, op, cfg, st);
     if (rc == -2 || rc == -3)
