@@ -541,6 +541,8 @@ def main():
     ap.add_argument("--cg-full", action="store_true",
                     help="also run the three CGs on the benchmark lattice (minutes)")
     args = ap.parse_args()
+    if not args.main_only and (args.prec != "f32" or args.nrhs != 1 or args.op != "dhop"):
+        ap.error("--prec, --nrhs and --op apply to --main-only runs")
     global DIMS, LS
     if args.dims:
         DIMS = tuple(int(v) for v in args.dims.split(","))
@@ -571,8 +573,6 @@ def main():
             print(json.dumps(out), flush=True)
         return 0
 
-    if not args.main_only and (args.prec != "f32" or args.nrhs != 1 or args.op != "dhop"):
-        ap.error("--prec, --nrhs and --op apply to --main-only runs")
     NR = args.nrhs
     prec = dw.DW_F16 if args.prec == "f16" else dw.DW_F32
     V4 = int(np.prod(DIMS))

@@ -61,3 +61,14 @@ def test_algorithmic_bytes_per_site_update():
     assert bench.bytes_per_site(4, 12) == 216.0
     assert bench.bytes_per_site(4, 12, 12) == 4 * (48 + 0.5)
     assert bench.bytes_per_site(8, 16) == 420.0
+
+
+def test_profiling_options_need_main_only():
+    # --op, --prec and --nrhs select what a profiling run (--main-only) times;
+    # the default benchmark line refuses them before touching the GPU
+    import subprocess
+    import sys
+    for extra in (["--op", "d"], ["--prec", "f16"], ["--nrhs", "2"]):
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + extra,
+                           capture_output=True, text=True, timeout=120)
+        assert r.returncode == 2 and "--main-only" in r.stderr, (extra, r.stderr[-300:])
