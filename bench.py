@@ -259,6 +259,40 @@ def cpu_baseline(psi, U, budget_s=12.0):
             "sample": "%d whole-lattice FP64 Dhop apply(s) at 32^3x64xLs12 (%.1f s each)" % (n, dt)}
 
 
+def oracle_timings(psi, U, budget_s=6.0):
+    """The FP64 oracle's D on the host cores at the benchmark lattice (whole-
+    lattice applies until the time budget is spent), and its CG on D^+D to 1e-10
+    at 4^4 x Ls=8 (the small lattice whose oracle CG finishes in a second):
+    context beside the GPU numbers, not a target."""
+    import oracle
+    from paper_2112_01852_gb300 import inputs
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.dw(psi, U, DIMS, LS, M5, B, C, [MF])
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = (time.perf_counter() - t0) / n
+    V5 = int(np.prod(DIMS)) * LS
+    dims1, ls1 = (4, 4, 4, 4), 8
+    U1 = inputs.exp_su3_field(dims1, seed=1)
+    b1 = inputs.gaussian_fermion(dims1, ls1, 1, seed=1)
+    t1 = time.perf_counter()
+    x1, iters, res = oracle.cg(b1, U1, dims1, ls1, M5, B, C, [MF], tol=1e-10)
+    cg_s = time.perf_counter() - t1
+    return {"cores": oracle.num_threads(), "kind": "oracle",
+            "D": {"value": FLOP_D_MOBIUS * V5 / dt / 1e9, "unit": "GFlop/s",
+                  "sample": "%d whole-lattice FP64 Moebius D apply(s) at %sxLs%d "
+                            "(%.1f s each)" % (n, "x".join(str(d) for d in DIMS), LS, dt)},
+            "cg_4x4x4x4_ls8": {"seconds": cg_s, "iters": int(_first(iters)),
+                               "resid": float(_first(res)), "tol": 1e-10}}
+
+
+def _first(v):
+    return v[0] if isinstance(v, (list, tuple, np.ndarray)) else v
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle on the same workload, each step a bounded
     sample of the lattice (a fixed set of 4D sites, all slices)."""
@@ -781,6 +815,7 @@ def main():
     line["paper_context"] = paper_context()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(psi, U)
+        line["oracle_timings"] = oracle_timings(psi, U)
     del x, y
     lat.close()
     if not args.no_cg:
