@@ -78,7 +78,7 @@ enum { DW_OP_DHOP = 0, DW_OP_DHOP_DAG = 1, DW_OP_D = 2, DW_OP_DDAG = 3, DW_OP_DD
 
 /*
  * Create a lattice of dims[4] = {Lx, Ly, Lz, Lt} 4D sites x Ls slices.
- * kind: DW_SHAMIR (b, c ignored and set to 1, 0) or DW_MOBIUS.
+ * kind: DW_SHAMIR (b, c ignored and set to 1, 0) or DW_MOBIUS (b nonzero).
  * prec: storage precision of the fields passed to the dw_apply_* calls
  *       (DW_F64, DW_F32, or DW_F16 = IEEE binary16 storage with FP32 arithmetic).
  * bc:   per-direction boundary sign (+1 periodic, -1 antiperiodic); NULL means

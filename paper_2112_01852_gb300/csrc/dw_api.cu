@@ -281,6 +281,9 @@ int dw_create_lattice(dw_lattice **out, const int dims[4], int Ls, int kind, dou
     if (!ok) return fail(DW_ERR_ARG, "Ls = %d unsupported (need Ls/spt <= 32 for spt in 1..4)", Ls);
   }
   if (kind != DW_SHAMIR && kind != DW_MOBIUS) return fail(DW_ERR_ARG, "unknown kind %d", kind);
+  // the D kernels form phi / b = psi + (c / b) K psi and scale the hop sum by b
+  if (kind == DW_MOBIUS && !(b != 0.0 && b == b && c == c))
+    return fail(DW_ERR_ARG, "Moebius b must be a nonzero number and c a number (b=%g c=%g)", b, c);
   if (prec != DW_F64 && prec != DW_F32 && prec != DW_F16)
     return fail(DW_ERR_ARG, "unknown precision %d", prec);
   if (bc)

@@ -483,6 +483,17 @@ __device__ __forceinline__ void half_axpby(Half<V2> &o, V2 a, const Half<V2> &x,
   }
 }
 
+// o = x + b y (the (b + cK) combination of D with b scaled out)
+template <class V2>
+__device__ __forceinline__ void half_axpy(Half<V2> &o, const Half<V2> &x, V2 b,
+                                         const Half<V2> &y) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o.re[c] = p_fma(b, y.re[c], x.re[c]);
+    o.im[c] = p_fma(b, y.im[c], x.im[c]);
+  }
+}
+
 // Rolling evaluation of A psi_s + B [K psi]_s (KDAG = false) or
 // A psi_s + B [K^+ psi]_s (KDAG = true) at 4D site x4 for s = s0 .. s0+SPT-1.
 //   K:   upper from s-1, lower from s+1;  K^+: upper from s+1, lower from s-1;
@@ -492,8 +503,9 @@ __device__ __forceinline__ void half_axpby(Half<V2> &o, V2 a, const Half<V2> &x,
 // HINT: the L2 policy of the loads (HINT_KEEP / HINT_DROP as for the hopping
 // term), or HINT_SMEM: F holds a staged copy of a slice range with both
 // neighbours of the range, slice s at index s - s0 + so (no wrap there); the
-// -mf factors still follow the global slice s and the global Ls.
-template <class P, bool KDAG, int SPT, int HINT = HINT_NONE, class Fn>
+// -mf factors still follow the global slice s and the global Ls.  UNIT: A = 1
+// (A is not read), psi_s + B [K psi]_s with one FMA per element.
+template <class P, bool KDAG, int SPT, int HINT = HINT_NONE, bool UNIT = false, class Fn>
 __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int Ls,
                                         typename P::C A, typename P::C B,
                                         typename P::C mf, Fn &&f, int so = 0) {
@@ -539,8 +551,13 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
     Spinor<V2> v;
     Half<V2> &vc = KDAG ? v.lo : v.up;
     Half<V2> &va = KDAG ? v.up : v.lo;
-    half_axpby(vc, vA, cur_carry, bc<V2>(B * (j == 0 ? fp : C(1))), prev);
-    half_axpby(va, vA, cur_ahead, bc<V2>(B * fn), next_ahead);
+    if constexpr (UNIT) {
+      half_axpy(vc, cur_carry, bc<V2>(B * (j == 0 ? fp : C(1))), prev);
+      half_axpy(va, cur_ahead, bc<V2>(B * fn), next_ahead);
+    } else {
+      half_axpby(vc, vA, cur_carry, bc<V2>(B * (j == 0 ? fp : C(1))), prev);
+      half_axpby(va, vA, cur_ahead, bc<V2>(B * fn), next_ahead);
+    }
     f(j, v);
     prev = cur_carry;
     cur_ahead = next_ahead;
@@ -549,7 +566,8 @@ __device__ __forceinline__ void roll_5d(const Field<P> &F, int x4, int s0, int L
 
 // One hop direction: acc[j] += (1 + S g_mu) W psi'(y4, s0 + j) for every j,
 // where W = U_mu(l4) (ADJ = false) or U_mu(l4)^+ (ADJ = true) and psi' is psi
-// itself (PHI = false) or phi = (b + cK) psi (PHI = true).  With PHI and
+// itself (PHI = false) or phi / b = psi + (c / b) K psi (PHI = true: the caller
+// passes c / b as `c`, b is not read, and scales the hop sum by b).  With PHI and
 // HINT_SMEM, F is a staged slice range (roll_5d's STG form; `so` the index of
 // global slice s0 there).
 template <class P, int MU, int S, bool ADJ, bool PHI, bool FIRST, int SPT, int HINT = HINT_NONE>
@@ -570,8 +588,8 @@ __device__ __forceinline__ void hop_dir(SpinorP<P> (&acc)[SPT],
   if constexpr (PHI) {
     // (the L2 eviction hints of the hopping term made D slower: 2.06 -> 2.34 ms
     // at 32^3 x 64 x 12; its global loads keep the default policy)
-    roll_5d<P, false, SPT, HINT == HINT_SMEM ? HINT_SMEM : HINT_NONE>(F, y4, s0, Ls, b, c, mf,
-                                                                    body, so);
+    roll_5d<P, false, SPT, HINT == HINT_SMEM ? HINT_SMEM : HINT_NONE, true>(F, y4, s0, Ls, b, c,
+                                                                          mf, body, so);
   } else {
     const unsigned long long pol = l2_policy<HINT>();
 #pragma unroll
@@ -840,8 +858,7 @@ __device__ __forceinline__ void hop_staged(Spinor<typename Pair<P>::type> (&acc)
         H.read_half(v.lo, stg, j * 6 * H.VPQ + 3 * H.VPQ);
         body(j, v);
       }
-    } else {
-      const V2 vb = bc<V2>(b);
+    } else {  // phi / b = psi + (c / b) K psi, as in hop_dir (`c` is c / b here)
 #pragma unroll
       for (int j = 0; j < SPT; ++j) {
         Half<V2> up_prev, up_cur, lo_cur, lo_next;
@@ -852,8 +869,8 @@ __device__ __forceinline__ void hop_staged(Spinor<typename Pair<P>::type> (&acc)
         const C fp = (j == 0 && s0 == 0) ? -mf : C(1);
         const C fn = (s0 + j + 1 == Ls) ? -mf : C(1);
         Spinor<V2> v;
-        half_axpby(v.up, vb, up_cur, bc<V2>(c * fp), up_prev);
-        half_axpby(v.lo, vb, lo_cur, bc<V2>(c * fn), lo_next);
+        half_axpy(v.up, up_cur, bc<V2>(c * fp), up_prev);
+        half_axpy(v.lo, lo_cur, bc<V2>(c * fn), lo_next);
         body(j, v);
       }
     }
@@ -979,10 +996,10 @@ __device__ __forceinline__ void halo_hop_down(Spinor<typename Pair<P>::type> (&a
 
 // Face halves a rank sends: to the rank below, the forward-hop projection of
 // its first t slice; to the rank above, U_t^+ times the backward-hop
-// projection of its last t slice.  PHI: the hop acts on phi = (b + cK) psi (the
-// operator D), formed at the face slices with the same arithmetic as roll_5d,
-// so the receiver's sums equal the undecomposed kernel's bit for bit.  One
-// thread per (face site, s) of one RHS.
+// projection of its last t slice.  PHI: the hop acts on phi / b = psi + (c/b) K psi
+// (the operator D; `c` is c / b here), formed at the face slices with the same
+// arithmetic as roll_5d, so the receiver's sums equal the undecomposed kernel's
+// bit for bit.  One thread per (face site, s) of one RHS.
 template <class P, bool PHI>
 __device__ __forceinline__ void face_spinor(Spinor<typename Pair<P>::type> &v, const Field<P> &F,
                                             int x4, int s, int Ls, typename P::C b,
@@ -994,7 +1011,7 @@ __device__ __forceinline__ void face_spinor(Spinor<typename Pair<P>::type> &v, c
     F.load_half(v.lo, x4, s, 1);
     return;
   }
-  // phi_s: upper = b u_s + c fp u_{s-1}, lower = b l_s + c fn l_{s+1}
+  // phi_s / b: upper = u_s + (c/b) fp u_{s-1}, lower = l_s + (c/b) fn l_{s+1}
   Half<V2> u, up, l, ln;
   const int sp = s == 0 ? Ls - 1 : s - 1;
   const int sn = s == Ls - 1 ? 0 : s + 1;
@@ -1004,8 +1021,8 @@ __device__ __forceinline__ void face_spinor(Spinor<typename Pair<P>::type> &v, c
   F.load_half(up, x4, sp, 0);
   F.load_half(l, x4, s, 1);
   F.load_half(ln, x4, sn, 1);
-  half_axpby(v.up, bc<V2>(b), u, bc<V2>(c * fp), up);
-  half_axpby(v.lo, bc<V2>(b), l, bc<V2>(c * fn), ln);
+  half_axpy(v.up, u, bc<V2>(c * fp), up);
+  half_axpy(v.lo, l, bc<V2>(c * fn), ln);
 }
 
 template <class P, bool DAG, bool PHI>
@@ -1029,7 +1046,7 @@ __global__ void halo_pack_kernel(typename P::vec *send_dn, typename P::vec *send
   F.V4 = V4;
   F.Ls = Ls;
   (void)plane;
-  const C b = (C)p.b, c = (C)p.c, mf = PHI ? (C)p.mf[rhs] : C(0);
+  const C b = (C)p.b, c = PHI ? (C)(p.c / p.b) : C(0), mf = PHI ? (C)p.mf[rhs] : C(0);
   {  // first slice -> rank below
     Spinor<V2> v;
     face_spinor<P, PHI>(v, F, face, s, Ls, b, c, mf);
@@ -1201,7 +1218,11 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   const vec *gauge = reinterpret_cast<const vec *>(p.gauge);
 
   const C mf = (OP == OP_D || OP == OP_DDAG) ? (C)p.mf[rhs] : C(0);
-  const C b = (C)p.b, c = (C)p.c;
+  // D's hop acts on phi / b = psi + (c / b) K psi: `c` is c / b for D, and the
+  // factor b moves into the scale of the hop sum (hsc), so forming the
+  // combination takes one FMA per element instead of an FMA and a multiply
+  const C b = (C)p.b, c = PHI ? (C)(p.c / p.b) : (C)p.c;
+  const C hsc = PHI ? (C)(p.hscale * p.b) : (C)p.hscale;
   const C alpha = (C)p.alpha, beta = (C)p.beta;
   // the field of the local term alpha psi + beta K psi (none: hopping term alone)
   Field<P> Fo;
@@ -1400,7 +1421,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
       if constexpr (OP == OP_D) {
         // the local term from the staged own site (the launch requires own = in)
         d_epilogue<P, SPT, true>(acc, out, xs, S, true, iat, sl + 1, s0, Ls, alpha, beta, mf,
-                                 bc<V2>((C)p.hscale), p.norm_partials != nullptr, nsq);
+                                 bc<V2>(hsc), p.norm_partials != nullptr, nsq);
         stored = true;
       } else if (RING) {
 #pragma unroll
@@ -1482,7 +1503,7 @@ __device__ __forceinline__ void dslash_body(const DslashParams &p) {
   auto store = [&](int j, const SpinorP<P> &v) {
     store_spinor<P>(out + F.site(s0 + j, xf), kPlaneStride, v);
   };
-  const V2 mhalf = bc<V2>((C)p.hscale);  // -1/2 of D_W, or the caller's factor
+  const V2 mhalf = bc<V2>(hsc);  // -1/2 of D_W (or the caller's factor), times b for D
 
   if constexpr (OP == OP_DHOP || OP == OP_DHOP_DAG) {
     if (active) {

@@ -32,3 +32,21 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
     # the Python binding resolves every symbol with its signature
     dw.load_library()
+
+
+def test_create_lattice_checks_its_arguments_before_any_device_call():
+    # argument errors come back as DW_ERR_ARG with a message, before the call
+    # touches a device (so this runs without a GPU): zero extents, an unknown
+    # kind, and a Moebius b of zero (the D kernels divide c by b)
+    import pytest
+    build.build()
+    cases = [((4, 0, 4, 4), 4, dw.DW_MOBIUS, 1.5, 0.5),
+             ((4, 4, 4, 4), 0, dw.DW_MOBIUS, 1.5, 0.5),
+             ((4, 4, 4, 4), 4, 7, 1.5, 0.5),
+             ((4, 4, 4, 4), 4, dw.DW_MOBIUS, 0.0, 0.5),
+             ((4, 4, 4, 4), 4, dw.DW_MOBIUS, float("nan"), 0.5)]
+    for dims, Ls, kind, b, c in cases:
+        with pytest.raises(dw.DWError) as e:
+            dw.dw_create_lattice(dims, Ls, kind, 1.8, b, c, dw.DW_F32)
+        assert e.value.code == dw.DW_ERR_ARG, (dims, Ls, kind, b)
+        assert dw.dw_last_error()
