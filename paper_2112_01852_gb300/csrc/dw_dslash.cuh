@@ -603,7 +603,8 @@ __device__ __forceinline__ void hop_dir(SpinorP<P> (&acc)[SPT],
 }
 
 // The D epilogue at output site xo, slices s0 .. s0+SPT-1:
-//   out = alpha psi + beta K psi + h acc   (h = hscale, -1/2 for D_W),
+//   out = alpha psi + beta K psi + h acc   (acc the hop sum of phi / b, h = b
+//   times hscale, which is -1/2 for D_W),
 // psi read from Fo at index io (STG: a staged slice range holding slice s0 at
 // index so, roll_5d's STG form; own false: no local term).  Adds |out|^2 to
 // nsq when `norm`.
