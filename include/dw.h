@@ -344,10 +344,10 @@ int dw_set_wait_polls(dw_lattice *lat, int polls);
  * iterated residual has fallen below delta times its largest value since the
  * previous update (Clark et al., mixed-precision solvers on GPUs; the paper
  * gives no solver).  0 < delta < 1 sets it; delta = 0 (the default) takes the
- * values measured fastest at 24^4 x Ls=16: for dw_cg_solve 1e-3 with FP32 and
- * 0.1 with FP16 inner fields, for dw_solve_eo 1e-4 and 0.01.  Smaller values
- * mean fewer FP64 operator applications, larger ones a shorter drift of the
- * iterated residual.
+ * values chosen from timings at 24^4 x Ls=16 and 32^3 x 64 x Ls=12: 1e-3 with
+ * FP32 inner fields, and with FP16 ones 0.1 for dw_cg_solve and 0.01 for
+ * dw_solve_eo.  Smaller values mean fewer FP64 operator applications, larger
+ * ones a shorter drift of the iterated residual.
  * Returns DW_OK or DW_ERR_ARG (delta outside [0, 1)).
  */
 int dw_set_reliable_delta(dw_lattice *lat, double delta);

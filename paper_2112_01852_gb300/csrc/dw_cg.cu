@@ -181,16 +181,17 @@ int cg_run(dw_lattice *lat, void *x, const void *b, const double *mf, int nrhs, 
            std::chrono::steady_clock::time_point t_start) {
   CGWork *w = lat->cg;
   cudaError_t e;
-  // reliable-update threshold (dw_set_reliable_delta), by default the fastest
-  // measured at 24^4 x 16 (every setting reaches the same residual): CG on D^+D
-  // 1e-3 with FP32 inner fields, 0.1 with FP16 ones (their rounding, 2^-11,
-  // makes the iterated residual drift further between updates); the even-odd
-  // solve, whose inner iterations are cheaper against its FP64 updates, 1e-4
-  // (FP32) and 0.01 (FP16)
+  // reliable-update threshold (dw_set_reliable_delta), by default chosen from
+  // timings at 24^4 x 16 and 32^3 x 64 x 12 (every setting reaches the same
+  // residual): 1e-3 with FP32 inner fields for both solvers; with FP16 ones
+  // (their rounding, 2^-11, makes the iterated residual drift further between
+  // updates) 0.1 for CG on D^+D and 0.01 for the even-odd solve, whose inner
+  // iterations are cheaper against its FP64 updates
   const double delta = mode == DW_F64                 ? 0.0
                        : lat->reliable_delta > 0.0 ? lat->reliable_delta
-                       : eo ? (mode == DW_F32 ? 1e-4 : 0.01)
-                            : (mode == DW_F32 ? 1e-3 : 0.1);
+                       : mode == DW_F32            ? 1e-3
+                       : eo                        ? 0.01
+                                                   : 0.1;
   Solve S{lat, w, nrhs, mode, mode == DW_F64 ? DW_F64 : DW_F32, delta,
           tol, maxit, mf, w->stream,
           BlasCtx((int)(eo ? lat->V4 / 2 : lat->V4), lat->Ls, nrhs, lat->num_sms), eo};
