@@ -72,3 +72,21 @@ def test_profiling_options_need_main_only():
         r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + extra,
                            capture_output=True, text=True, timeout=120)
         assert r.returncode == 2 and "--main-only" in r.stderr, (extra, r.stderr[-300:])
+
+
+def test_kernel_digest_follows_code_not_comments(tmp_path, monkeypatch):
+    # the traffic record is voided by a change of the stencil code, not by an
+    # edited comment or reflowed whitespace
+    csrc = tmp_path / "paper_2112_01852_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / "dw_common.cuh").write_text("// common\nstruct A { int x; };\n")
+    (csrc / "dw_dslash.cuh").write_text("/* kernel */\nint f(int a) { return a + 1; }\n")
+    (csrc / "dw_api.cu").write_text("int host_side() { return 0; }\n")
+    d0 = bench.kernel_digest()
+    (csrc / "dw_dslash.cuh").write_text("/* the kernel, reworded */\nint f(int a)\n"
+                                        "{  return a + 1;  // same code\n}\n")
+    (csrc / "dw_api.cu").write_text("int host_side() { return 1; }\n")  # not a stencil file
+    assert bench.kernel_digest() == d0
+    (csrc / "dw_dslash.cuh").write_text("int f(int a) { return a + 2; }\n")
+    assert bench.kernel_digest() != d0
