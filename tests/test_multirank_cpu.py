@@ -145,3 +145,43 @@ def test_gloo_data_plane_and_distributed_cg(world):
         assert red == [sum(range(1, world + 1)) * 1.0, float(2 ** world - 1)]
         assert all(conv) and max(res) <= 1e-12 and 0 < iters <= 500
         assert np.allclose(x, want, rtol=0, atol=1e-10)
+
+
+def test_mixed_cg_single_process_edge_cases():
+    # defect correction on one process (no torch.distributed): an RHS that is
+    # already solved gets a zero correction and stays converged, an iteration
+    # budget too small to converge reports not converged, and a zero RHS is
+    # solved by x = 0
+    import numpy as np
+    import torch
+    from paper_2112_01852_gb300 import dist
+
+    class LocalComm:
+        def exchange(self, send_dn, send_up, recv_up, recv_dn):
+            recv_up.copy_(send_dn)  # one rank: both neighbours are itself
+            recv_dn.copy_(send_up)
+
+        def allreduce(self, values):
+            return list(values)
+
+    n, nrhs, m2 = 16, 3, 0.3
+    hi = _ring_ops(LocalComm(), n, nrhs, m2)
+    lo = _ring_ops(LocalComm(), n, nrhs, m2, torch.float32)
+    A = (m2 + 2.0) * np.eye(n) - np.roll(np.eye(n), 1, axis=1) - np.roll(np.eye(n), -1, axis=1)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal((nrhs, n))
+    b[2] = 0.0                                   # a zero right-hand side
+    x = hi.new()
+    x[1] = torch.from_numpy(np.linalg.solve(A, b[1]))  # RHS 1 starts solved
+    bt = torch.from_numpy(b)
+    conv, iters, outer, res = dist.mixed_cg(hi, lo, lambda o, i: o.copy_(i),
+                                            lambda o, i: o.copy_(i), x, bt, nrhs, 1e-12, 500,
+                                            inner_tol=1e-4)
+    assert all(conv) and max(res) <= 1e-12, res
+    assert np.allclose(x.numpy()[:2], np.linalg.solve(A, b[:2].T).T, rtol=0, atol=1e-10)
+    assert np.all(x.numpy()[2] == 0.0)
+    x2 = hi.new()
+    conv2, iters2, _, res2 = dist.mixed_cg(hi, lo, lambda o, i: o.copy_(i),
+                                           lambda o, i: o.copy_(i), x2, bt, nrhs, 1e-12, 2,
+                                           inner_tol=1e-4)
+    assert iters2 <= 4 and not conv2[0] and res2[0] > 1e-12
